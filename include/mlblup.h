@@ -1,0 +1,182 @@
+/*
+ * mlblup.h -- C ABI of the GB300 multilevel BLUP library (libmlblup.so).
+ *
+ * The library computes the multilevel best linear unbiased predictor of
+ * Castrillon-Candas, "Spatial best linear unbiased prediction: a computational
+ * mathematics approach for high dimensional massive datasets" (arXiv:1701.00285):
+ *
+ *   model       Z = X beta + eps, eps ~ N(0, C(theta))          (Sec. 2, eq. vectormodel)
+ *   basis       kd-tree + multilevel basis W, with W X = 0      (Sec. 3.1, Algs. 1-3, steps 1-5)
+ *   assembly    C~_W = entries psi^T C psi within distance tau  (Sec. 4, Algs. 4-7)
+ *   solve       C~_W gamma_W = W Z by diagonal PCG, gamma = W^T gamma_W,
+ *               beta = (X^T X)^{-1} X^T (Z - C gamma)            (Sec. 5.2, eqs. Spatial:eqn1-3; Sec. 6.2)
+ *   predict     Z(x0) = k(x0)^T beta + c(x0)^T gamma            (Sec. 5.2, eq. Spatial)
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an mlb_status; no exception crosses the ABI.  On error
+ *    mlb_last_error(ctx) returns a message that stays valid until the next call.
+ *  - Points are row-major double arrays (N x d), in the caller's order; every
+ *    vector in or out (Z, gamma, predictions) is in the caller's order.  The
+ *    kd-tree permutation is internal.
+ *  - The caller owns every buffer it passes; the library copies inputs and
+ *    writes outputs before returning (host variants) or in stream order on
+ *    the context's stream (_dev variants, which take device pointers and do
+ *    not synchronise).  The context owns all device memory it allocates.
+ *  - Call order: mlb_build_basis -> mlb_assemble -> mlb_solve -> mlb_predict
+ *    or mlb_grad.  A call made before its prerequisite returns MLB_ESTATE.
+ *    A new mlb_build_basis invalidates the assembly and the solution; a new
+ *    mlb_assemble invalidates the solution.
+ *  - Matern smoothness nu must be 0.5, 1.5 or 2.5 (closed forms of the
+ *    definition in Sec. 3.1); unit variance; the nugget is added on the data
+ *    diagonal only.
+ *  - beta is reported on the library's monomial basis: total degree <= w,
+ *    graded order, lexicographically decreasing exponents within a degree
+ *    (1, x1, .., xd, x1^2, x1 x2, ..), evaluated on coordinates mapped onto
+ *    [-1, 1]^d by the bounding box of the data points.
+ */
+#ifndef MLBLUP_H
+#define MLBLUP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MLB_ABI_VERSION 1
+
+typedef struct mlb_ctx mlb_ctx;
+
+typedef enum {
+    MLB_OK = 0,
+    MLB_EINVAL = 1,      /* bad argument (sizes, nu, NULL pointer, unsupported option) */
+    MLB_ERANK = 2,       /* a local moment matrix or X is rank deficient (Sec. 2: X full column rank) */
+    MLB_ENOCONV = 3,     /* PCG reached pcg_maxit before the tolerance */
+    MLB_EBREAKDOWN = 4,  /* PCG found p^T A p <= 0 (truncated C~_W not positive definite) */
+    MLB_ENOMEM = 5,      /* device allocation failed */
+    MLB_ECUDA = 6,       /* a CUDA call failed (message has the CUDA error string) */
+    MLB_ETIMEOUT = 7,    /* a bounded device wait gave up */
+    MLB_ESTATE = 8       /* call made out of order */
+} mlb_status;
+
+enum { MLB_FP64 = 0, MLB_MIXED = 1 };
+
+typedef struct {
+    int precision;     /* MLB_FP64: every step in FP64.  MLB_MIXED: kernel tiles and
+                          kernel sums in FP32 (FP64 accumulation across tiles), basis,
+                          PCG vectors, inner products and the p x p trend solve in FP64 */
+    int leaf_size;     /* kd-tree leaf size n0 (cells split while they hold more than n0 points) */
+    double pcg_rtol;   /* stop when ||Z_W - C~_W g||_2 <= pcg_rtol ||Z_W||_2 (Sec. 6.2, remark) */
+    int pcg_maxit;     /* iteration cap */
+    int precond;       /* 1: P_W = diag(C~_W) (Sec. 5.2 remark); 0: P_W = I */
+    int matrix_free;   /* 0: assembled C~_W; 1: three-step product W (C (W^T g)) (Sec. 6.2),
+                          which needs tau = inf and keeps no matrix */
+    int device;        /* CUDA device ordinal */
+} mlb_opts;
+
+typedef struct {
+    double nu;         /* Matern smoothness: 0.5, 1.5 or 2.5 */
+    double rho;        /* Matern range (> 0) */
+    double nugget;     /* eta >= 0, added to the covariance of the observations */
+} mlb_theta;
+
+typedef struct {
+    int iterations;            /* PCG iterations */
+    int converged;             /* 1 if the tolerance was met */
+    double rel_residual;       /* ||r_k|| / ||Z_W|| of the recursive PCG residual */
+    int64_t nnz;               /* stored entries of C~_W (both triangles) */
+    int64_t blocks;            /* stored cell-pair blocks (both triangles) */
+    double ms_assemble;        /* device time of the last mlb_assemble */
+    double ms_pcg;             /* device time of the PCG loop */
+    double ms_beta;            /* device time of gamma = W^T g and the beta step */
+} mlb_info;
+
+/* Fills *opts with defaults: FP64, n0 = 64, rtol 1e-10, maxit 20000, diagonal
+ * preconditioner, assembled matrix, device 0. */
+void mlb_default_opts(mlb_opts* opts);
+
+/* Creates a context on opts->device with its own CUDA stream.
+ * Errors: MLB_EINVAL (bad options), MLB_ECUDA. */
+mlb_status mlb_create(const mlb_opts* opts, mlb_ctx** out);
+
+/* Frees every device buffer of the context.  NULL is accepted. */
+void mlb_destroy(mlb_ctx* ctx);
+
+const char* mlb_last_error(const mlb_ctx* ctx);
+const char* mlb_status_string(mlb_status s);
+
+/* Replaces the context's stream by a caller-owned cudaStream_t (NULL: back
+ * to the context's own stream).  Later calls enqueue their kernels there. */
+mlb_status mlb_set_stream(mlb_ctx* ctx, void* cuda_stream);
+
+/* Kd-tree (Algs. 1-3) and multilevel basis (Sec. 3.1, steps 1-5) of N points
+ * in d dimensions with the total-degree-w trend space, p = binom(d+w, w).
+ * points: host, N x d row-major.  Needs N > p.  The basis is built in FP64:
+ * each cell's orthonormal split of its moment matrix X^T B into scaling and
+ * wavelet vectors comes from a Householder QR.  MLB_ERANK if some local
+ * moment matrix is not of full rank min(p, s) (points not in general position). */
+mlb_status mlb_build_basis(mlb_ctx* ctx, const double* points, int64_t N, int d, int w);
+/* Same with points in device memory. */
+mlb_status mlb_build_basis_dev(mlb_ctx* ctx, const double* points_dev, int64_t N, int d, int w);
+
+/* Sparse multilevel covariance C~_W (Sec. 4, Algs. 4-7) for theta.  A cell
+ * pair (m, q) is kept when the bounding box of q's points meets the box of
+ * m's points grown by tau_mq = tau_factor * sqrt(D_m D_q) on every axis (D =
+ * box diagonal); tau_factor = INFINITY keeps every pair.  Also forms
+ * P_W = diag(C~_W).  With opts.matrix_free = 1 only theta is recorded (tau_factor
+ * must be INFINITY).  MLB_EINVAL: bad theta, leaf_size or 2p above 64 on the
+ * assembled path. */
+mlb_status mlb_assemble(mlb_ctx* ctx, const mlb_theta* theta, double tau_factor);
+
+/* Solves for gamma and beta (eqs. Spatial:eqn2-3).  Z: host, N.  beta_out:
+ * host, p entries, may be NULL.  info may be NULL.  MLB_ENOCONV / MLB_EBREAKDOWN
+ * leave the last iterate in place (predict still works). */
+mlb_status mlb_solve(mlb_ctx* ctx, const double* Z, double* beta_out, mlb_info* info);
+/* Same with Z and beta_out in device memory (beta_out may be NULL). */
+mlb_status mlb_solve_dev(mlb_ctx* ctx, const double* Z_dev, double* beta_dev, mlb_info* info);
+
+/* Predictions at M targets (eq. Spatial).  targets: host M x d; yhat_out: host M. */
+mlb_status mlb_predict(mlb_ctx* ctx, const double* targets, int64_t M, double* yhat_out);
+mlb_status mlb_predict_dev(mlb_ctx* ctx, const double* targets_dev, int64_t M, double* yhat_dev);
+
+/* Held-out loss L = mean_k (yhat_k - y_k)^2 and its derivatives in log(rho) and
+ * log(nugget) by the adjoint of the saddle-point system (eq. Spatial:problem);
+ * the adjoint is solved with the same multilevel PCG and the derivative blocks
+ * dC/dlog(rho) are contracted on the fly, never stored.  Requires a solve.
+ * Host pointers; any of the three outputs may be NULL. */
+mlb_status mlb_grad(mlb_ctx* ctx, const double* targets, int64_t M, const double* y_obs,
+                    double* loss_out, double* dlogrho_out, double* dlognugget_out);
+
+/* ---- inspection (tests and tools) ---------------------------------------- */
+
+/* Sizes of the current basis.  Any pointer may be NULL. */
+mlb_status mlb_get_sizes(const mlb_ctx* ctx, int64_t* N, int* d, int* p, int* t, int64_t* nwav);
+
+/* perm[i] = caller index of the point at kd-tree position i (host, N entries). */
+mlb_status mlb_get_perm(mlb_ctx* ctx, int32_t* perm);
+
+/* gamma-hat of the last solve, caller order (host, N). */
+mlb_status mlb_get_gamma(mlb_ctx* ctx, double* gamma);
+
+/* out = W v (host, N -> N-p) and out = W^T u (host, N-p -> N). */
+mlb_status mlb_apply_W(mlb_ctx* ctx, const double* v, double* out);
+mlb_status mlb_apply_Wt(mlb_ctx* ctx, const double* u, double* out);
+
+/* out = C~_W u with the assembled matrix (or the three-step product). Host, N-p. */
+mlb_status mlb_cw_matvec(mlb_ctx* ctx, const double* u, double* out);
+
+/* Pattern of the assembled matrix: flags[m * n_j + q] = 1 if cell m of level i
+ * and cell q of level j form a stored block (host buffer of 2^i * 2^j bytes). */
+mlb_status mlb_get_pattern(mlb_ctx* ctx, int i, int j, uint8_t* flags);
+
+/* Kernel sum out_k = sum_j phi(|x0_k - x_j|) a_j over the data points (no
+ * nugget): the primitive behind C gamma and c(x0)^T gamma.  Host pointers;
+ * a in caller order. */
+mlb_status mlb_kernel_sum(mlb_ctx* ctx, const double* targets, int64_t M, const double* a,
+                          double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLBLUP_H */

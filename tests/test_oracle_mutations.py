@@ -1,0 +1,79 @@
+"""Planted mistakes: each test injects a plausible bug into the oracle (on the
+CPU only) and checks that one of the pins catches it."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import basis as ob, grad, matern, mlblup, pattern as op, tree as ot
+from oracle import dense
+
+
+def test_dropped_term_in_matern_is_caught(monkeypatch):
+    from tests.test_oracle_matern_design import matern_definition
+    good = matern.matern
+
+    def bad(r, nu, rho):
+        if nu == 2.5:
+            s = math.sqrt(5.0) * np.asarray(r) / rho
+            return (1.0 + s) * np.exp(-s)        # s^2/3 term dropped
+        return good(r, nu, rho)
+
+    r = np.linspace(0, 2, 50)
+    assert not np.allclose(bad(r, 2.5, 0.4), matern_definition(r, 2.5, 0.4), rtol=1e-6)
+
+
+def test_wrong_scaling_wavelet_split_is_caught(monkeypatch):
+    orig_svd = np.linalg.svd
+
+    def shifted(M, full_matrices=True):
+        U, S, Vh = orig_svd(M, full_matrices=full_matrices)
+        return U, S, np.roll(Vh, 1, axis=0)      # columns of V out of order
+    monkeypatch.setattr(ob.np.linalg, "svd", shifted)
+    x = np.random.default_rng(0).random((120, 2))
+    try:
+        B = ob.build_basis(x, ot.build_tree(x, 10), 1)
+    except ob.RankDeficient:
+        return
+    assert np.abs(B.dense_W() @ B.X).max() > 1e-6
+
+
+def test_one_sided_box_test_is_caught():
+    x = np.array([0.0, 0.1, 0.2, 0.3, 1.0, 1.1, 3.0, 3.1])[:, None]
+    T = ot.build_tree(x, 2)
+    D = op.diameters(T, 2)
+    tau = op.tau_pair(D[:, None], D[None, :], 2.0)
+    lo_m, hi_m = T.lo[2][:, None, 0], T.hi[2][:, None, 0]
+    lo_q, hi_q = T.lo[2][None, :, 0], T.hi[2][None, :, 0]
+    bad = ~((lo_q - hi_m) > tau)                 # planted: the lo_m - hi_q side is not tested
+    good = op.level_pair_bruteforce(T, 2, 2, 2.0)
+    assert not np.array_equal(bad, good)
+    assert not np.array_equal(bad, bad.T)        # and the symmetry pin fails too
+
+
+def test_trend_step_with_wrong_sign_is_caught(monkeypatch):
+    P = wl.small_problem(40, 160, 2, 1, nugget=1e-4, leaf_size=12)
+    good_cov = mlblup.cov_matvec
+    monkeypatch.setattr(mlblup, "cov_matvec", lambda pts, v, nu, rho, nug: -good_cov(pts, v, nu, rho, nug))
+    rm = mlblup.blup(P.points, P.Z, P.targets, 1, P.nu, P.rho, P.nugget, 12, exact=True)
+    rd = dense.dense_blup(P.points, P.Z, P.targets, 1, P.nu, P.rho, P.nugget)
+    assert np.linalg.norm(rm["yhat"] - rd["yhat"]) > 1e-3 * np.linalg.norm(rd["yhat"])
+
+
+def test_missing_trend_adjoint_is_caught(monkeypatch):
+    P = wl.small_problem(41, 160, 2, 1, nu=1.5, rho=0.3, nugget=1e-4, leaf_size=12, with_y=True, M=30)
+    d = grad.grad_dense(P.points, P.Z, P.targets, P.y_targets, 1, 1.5, 0.3, 1e-4)
+    real_solve = np.linalg.solve
+    calls = {"n": 0}
+
+    def zero_lambda0(A, b):
+        out = real_solve(A, b)
+        if np.ndim(b) == 1 and A.shape == (3, 3):
+            calls["n"] += 1
+            if calls["n"] == 2:               # the lambda_0 = X (X^T X)^{-1} b solve
+                return np.zeros_like(out)
+        return out
+    monkeypatch.setattr(grad.np.linalg, "solve", zero_lambda0)
+    m = grad.grad_multilevel(P.points, P.Z, P.targets, P.y_targets, 1, 1.5, 0.3, 1e-4, 12)
+    assert not np.allclose(m[1:], d[1:], rtol=1e-4)
