@@ -89,6 +89,8 @@ typedef struct {
     double ms_assemble;        /* device time of the last mlb_assemble */
     double ms_pcg;             /* device time of the PCG loop */
     double ms_beta;            /* device time of gamma = W^T g and the beta step */
+    int64_t nnz_unique;        /* entries of the blocks j >= i (each symmetric pair once) */
+    int64_t launches;          /* kernels this context has launched since mlb_create */
 } mlb_info;
 
 /* Fills *opts with defaults: FP64, n0 = 64, rtol 1e-10, maxit 20000, diagonal
@@ -164,6 +166,12 @@ mlb_status mlb_apply_Wt(mlb_ctx* ctx, const double* u, double* out);
 
 /* out = C~_W u with the assembled matrix (or the three-step product). Host, N-p. */
 mlb_status mlb_cw_matvec(mlb_ctx* ctx, const double* u, double* out);
+/* Same on device buffers (N-p doubles each), enqueued on the context's stream:
+ * the very product one PCG iteration performs. */
+mlb_status mlb_cw_matvec_dev(mlb_ctx* ctx, const double* u_dev, double* out_dev);
+
+/* Number of kernels the context has launched since mlb_create. */
+mlb_status mlb_get_launch_count(const mlb_ctx* ctx, int64_t* count);
 
 /* Pattern of the assembled matrix: flags[m * n_j + q] = 1 if cell m of level i
  * and cell q of level j form a stored block (host buffer of 2^i * 2^j bytes). */

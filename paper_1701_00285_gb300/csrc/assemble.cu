@@ -1,0 +1,451 @@
+// Sparse multilevel covariance C~_W (Sec. 4, Algorithms 4-7) on the GPU.
+//
+// Alg. 7 evaluates every stored entry psi^T C psi directly, which costs a
+// kernel block of n_m x n_q evaluations for each admissible pair of cells at
+// every level pair -- about N^2 evaluations per coarse level pair.  Here the
+// same entries come from the two-scale relations of the basis (Sec. 3.1: a
+// cell's scaling and wavelet vectors are [phi_L 0; 0 phi_R] V):
+//
+//  1. leaf pass: for every pair of leaves (f <= e), G = V_f^T C(S_f, S_e) V_e with
+//     C evaluated on the fly (nugget on coinciding points).  Its
+//     wavelet-wavelet part is the (t, t) block of C_W; its scaling-scaling
+//     part SS and scaling-wavelet part SW feed the coarser levels;
+//  2. level pass, l = t-1 .. 0: for every pair of cells (c <= d) of level l,
+//     G = V_c^T H V_d where H is the 2x2 arrangement of the children's SS
+//     blocks; again WW -> block (l, l) of C_W, SS and SW -> next level;
+//  3. cross-level pass: for j = t .. 1 the rows of SW_j (scaling functions of
+//     level j against wavelets of level j) are carried up the tree with the
+//     factors V of levels j-1 .. 0; the wavelet rows that appear at level l are
+//     the blocks (l, j) of C_W.
+//
+// The result equals psi^T C psi for every entry (same definition, different
+// association order); only admissible blocks (distance criterion of Sec. 4.1,
+// see the pattern kernels) are stored.  The kernel is evaluated once per pair
+// of points, N^2 / 2 times in all, instead of once per pair per level pair.
+//
+// Storage: one dense row panel per cell (k_c rows, the admissible blocks side
+// by side in global column order) plus one column-index list per panel.
+#include <cmath>
+
+#include "internal.h"
+#include "matern.cuh"
+
+namespace mlb {
+
+struct PatArgs {
+    const double* lo;
+    const double* hi;
+    const double* diam;
+    int d;
+    int inf;
+    double c;
+};
+
+// Distance criterion: the box of q meets the box of m grown by
+// tau = c sqrt(D_m D_q) on every axis (symmetric in m and q).
+__device__ __forceinline__ bool admissible(const PatArgs& P, int gm, int gq) {
+    if (P.inf) return true;
+    const double tau = __dmul_rn(P.c, sqrt(__dmul_rn(P.diam[gm], P.diam[gq])));
+    for (int k = 0; k < P.d; ++k) {
+        if (__dsub_rn(P.lo[gq * P.d + k], P.hi[gm * P.d + k]) > tau) return false;
+        if (__dsub_rn(P.lo[gm * P.d + k], P.hi[gq * P.d + k]) > tau) return false;
+    }
+    return true;
+}
+
+__global__ void count_kernel(PatArgs P, CellTables C, int ncell, int* ncols, int* nblk) {
+    const int gm = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gm >= ncell) return;
+    int cols = 0, nb = 0;
+    if (C.k[gm] > 0) {
+        for (int gq = lane; gq < ncell; gq += 32) {
+            const int kq = C.k[gq];
+            if (kq > 0 && admissible(P, gm, gq)) {
+                cols += kq;
+                nb += 1;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        cols += __shfl_xor_sync(0xffffffffu, cols, o);
+        nb += __shfl_xor_sync(0xffffffffu, nb, o);
+    }
+    if (lane == 0) {
+        ncols[gm] = cols;
+        nblk[gm] = nb;
+    }
+}
+
+// Column lists and the block-column table, columns in global wavelet order.
+__global__ void fill_kernel(PatArgs P, CellTables C, int ncell, const int* __restrict__ colOrder,
+                            Panels pan) {
+    const int gm = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gm >= ncell) return;
+    const bool rowOk = C.k[gm] > 0;
+    int base = 0;
+    int* brow = pan.bcol + (int64_t)gm * ncell;
+    int* cols = pan.colidx + (rowOk ? pan.colOff[gm] : 0);
+    for (int q0 = 0; q0 < ncell; q0 += 32) {
+        const int q = q0 + lane;
+        int gq = -1, kk = 0;
+        bool ok = false;
+        if (q < ncell) {
+            gq = colOrder[q];
+            const int kq = C.k[gq];
+            ok = rowOk && kq > 0 && admissible(P, gm, gq);
+            kk = ok ? kq : 0;
+        }
+        int incl = kk;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int excl = base + incl - kk;
+        if (q < ncell) {
+            brow[gq] = ok ? excl : -1;
+            if (ok) {
+                const int64_t w0 = C.wOff[gq];
+                for (int i = 0; i < kk; ++i) cols[excl + i] = (int)(w0 + i);
+            }
+        }
+        base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+}
+
+struct TileOut {
+    double* SS;          // this level's SS matrix (sumA x sumA, row-major)
+    double* SW;          // this level's SW matrix (sumA x sumK, row-major)
+    int64_t ldSS, ldSW;
+    Panels pan;
+    int ncell;
+};
+
+struct TileIn {
+    const double* V;     // pool of the cells' orthogonal factors
+    // leaf pass: kernel block on the fly
+    const double* xs;
+    int d, kind;
+    double scale, nugget;
+    // level pass: children's SS matrix
+    const double* SSc;
+    int64_t ldSSc;
+};
+
+__device__ __forceinline__ void unrank_pair(int64_t pi, int& f, int& e) {
+    int64_t ee = (int64_t)((sqrt(8.0 * (double)pi + 1.0) - 1.0) * 0.5);
+    while ((ee + 1) * (ee + 2) / 2 <= pi) ++ee;
+    while (ee * (ee + 1) / 2 > pi) --ee;
+    e = (int)ee;
+    f = (int)(pi - ee * (ee + 1) / 2);
+}
+
+// Writes one entry G[r][c] of the pair (f, e) of one level to SS, SW and the
+// panels, with the mirrored copies for f != e.
+__device__ __forceinline__ void put_entry(const CellTables& C, const TileOut& o, int gf, int ge,
+                                          bool diagPair, int af, int ae, int r, int c, double v) {
+    if (r < af) {
+        if (c < ae) {
+            o.SS[(C.sOff[gf] + r) * o.ldSS + C.sOff[ge] + c] = v;
+            if (!diagPair) o.SS[(C.sOff[ge] + c) * o.ldSS + C.sOff[gf] + r] = v;
+        } else {
+            o.SW[(C.sOff[gf] + r) * o.ldSW + C.wLoc[ge] + (c - ae)] = v;
+        }
+    } else if (c < ae) {
+        if (!diagPair) o.SW[(C.sOff[ge] + c) * o.ldSW + C.wLoc[gf] + (r - af)] = v;
+    } else {
+        const int bc = o.pan.bcol[(int64_t)gf * o.ncell + ge];
+        if (bc >= 0) {
+            o.pan.vals[o.pan.valOff[gf] + (int64_t)(r - af) * o.pan.ncols[gf] + bc + (c - ae)] = v;
+            if (!diagPair) {
+                const int bt = o.pan.bcol[(int64_t)ge * o.ncell + gf];
+                o.pan.vals[o.pan.valOff[ge] + (int64_t)(c - ae) * o.pan.ncols[ge] + bt + (r - af)] = v;
+            }
+        }
+    }
+}
+
+// G = V_f^T H V_e for every pair f <= e of one level (tiles up to 64 x 64,
+// 256 threads, 4 x 4 register micro-tiles).  H is the covariance block of the
+// two leaves (LEAF) or the children's SS blocks (coarser levels).
+template <bool LEAF>
+__global__ void __launch_bounds__(256) galerkin_tile_kernel(CellTables C, int level, int64_t npairs,
+                                                            TileIn in, TileOut out) {
+    constexpr int S = kTile;
+    extern __shared__ double sm[];
+    double* Vf = sm;
+    double* Ve = Vf + S * S;
+    double* P = Ve + S * S;
+    double* xf = P + S * S;
+    double* xe = xf + S * kMaxDim;
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+    const int r0 = ty * 4, c0 = tx * 4;
+    const int first = (1 << level) - 1;
+    for (int64_t pi = blockIdx.x; pi < npairs; pi += gridDim.x) {
+        int f, e;
+        unrank_pair(pi, f, e);
+        const int gf = first + f, ge = first + e;
+        const int sf = C.s[gf], se = C.s[ge], af = C.a[gf], ae = C.a[ge];
+        const double* gVf = in.V + C.vOff[gf];
+        const double* gVe = in.V + C.vOff[ge];
+        for (int idx = tid; idx < S * S; idx += 256) {
+            const int r = idx / S, c = idx % S;
+            Vf[idx] = (r < sf && c < sf) ? gVf[r * sf + c] : 0.0;
+            Ve[idx] = (r < se && c < se) ? gVe[r * se + c] : 0.0;
+        }
+        if (LEAF) {
+            const int d = in.d;
+            const int64_t bf = C.beg[gf], be = C.beg[ge];
+            for (int idx = tid; idx < sf * d; idx += 256) xf[idx] = in.xs[bf * d + idx];
+            for (int idx = tid; idx < se * d; idx += 256) xe[idx] = in.xs[be * d + idx];
+        }
+        __syncthreads();
+        // H
+        if (LEAF) {
+            const int d = in.d;
+            for (int idx = tid; idx < S * S; idx += 256) {
+                const int r = idx / S, c = idx % S;
+                double v = 0.0;
+                if (r < sf && c < se) {
+                    double r2 = 0.0;
+                    for (int k = 0; k < d; ++k) {
+                        const double df = xf[r * d + k] - xe[c * d + k];
+                        r2 += df * df;
+                    }
+                    v = matern_f64(sqrt(r2), in.kind, in.scale);
+                    if (gf == ge && r == c) v += in.nugget;
+                }
+                P[idx] = v;
+            }
+        } else {
+            const int64_t row0 = C.sOff[2 * gf + 1], col0 = C.sOff[2 * ge + 1];
+            for (int idx = tid; idx < S * S; idx += 256) {
+                const int r = idx / S, c = idx % S;
+                P[idx] = (r < sf && c < se) ? in.SSc[(row0 + r) * in.ldSSc + col0 + c] : 0.0;
+            }
+        }
+        __syncthreads();
+        // T = H V_e
+        double acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int k = 0; k < S; ++k) {
+            double a4[4], b4[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a4[i] = P[(r0 + i) * S + k];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b4[j] = Ve[k * S + c0 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a4[i] * b4[j];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) P[(r0 + i) * S + c0 + j] = acc[i][j];
+        __syncthreads();
+        // G = V_f^T T
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int k = 0; k < S; ++k) {
+            double a4[4], b4[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a4[i] = Vf[k * S + r0 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b4[j] = P[k * S + c0 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a4[i] * b4[j];
+        }
+        const bool diagPair = (gf == ge);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = r0 + i, c = c0 + j;
+                if (r < sf && c < se) put_entry(C, out, gf, ge, diagPair, af, ae, r, c, acc[i][j]);
+            }
+        __syncthreads();
+    }
+}
+
+// One step of the cross-level pass: rows of X_{l+1} (scaling functions of
+// level l+1 against the wavelets of level j) -> V_c^T per cell c of level l.
+// Scaling rows go to X_l, wavelet rows are the blocks (c, e) of C_W.
+__global__ void __launch_bounds__(128) cross_kernel(CellTables C, const double* __restrict__ Vpool,
+                                                    int level, int jlevel, const double* __restrict__ Xin,
+                                                    double* __restrict__ Xout, int64_t ldX,
+                                                    int64_t levelBaseJ, Panels pan, int ncell) {
+    extern __shared__ double sm[];
+    const int g = (1 << level) - 1 + blockIdx.x;
+    const int s = C.s[g], a = C.a[g];
+    double* Vc = sm;
+    double* inb = Vc + s * s;
+    const int tid = threadIdx.x;
+    const int64_t col = (int64_t)blockIdx.y * 128 + tid;
+    const double* gV = Vpool + C.vOff[g];
+    for (int idx = tid; idx < s * s; idx += 128) Vc[idx] = gV[idx];
+    const int64_t row0 = C.sOff[2 * g + 1];
+    if (col < ldX)
+        for (int i = 0; i < s; ++i) inb[i * 128 + tid] = Xin[(row0 + i) * ldX + col];
+    __syncthreads();
+    if (col >= ldX) return;
+    const int ge = pan.rowCell[levelBaseJ + col];
+    const int cl = (int)(levelBaseJ + col - C.wOff[ge]);
+    const int bc = pan.bcol[(int64_t)g * ncell + ge];
+    const int bt = bc >= 0 ? pan.bcol[(int64_t)ge * ncell + g] : -1;
+    for (int j = 0; j < s; ++j) {
+        if (j >= a && bc < 0) break;
+        double acc = 0.0;
+        for (int i = 0; i < s; ++i) acc += Vc[i * s + j] * inb[i * 128 + tid];
+        if (j < a) {
+            if (level > 0) Xout[(C.sOff[g] + j) * ldX + col] = acc;
+        } else {
+            pan.vals[pan.valOff[g] + (int64_t)(j - a) * pan.ncols[g] + bc + cl] = acc;
+            pan.vals[pan.valOff[ge] + (int64_t)cl * pan.ncols[ge] + bt + (j - a)] = acc;
+        }
+    }
+}
+
+__global__ void diag_kernel(CellTables C, Panels pan, int ncell, int64_t nwav, double* diag) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= nwav) return;
+    const int g = pan.rowCell[r];
+    const int i = (int)(r - C.wOff[g]);
+    const int bc = pan.bcol[(int64_t)g * ncell + g];
+    diag[r] = pan.vals[pan.valOff[g] + (int64_t)i * pan.ncols[g] + bc + i];
+}
+
+mlb_status assemble_dev(mlb_ctx* ctx) {
+    cudaStream_t st = ctx->stream;
+    const int ncell = ctx->ncell, t = ctx->t;
+    PatArgs P;
+    P.lo = ctx->cells.lo;
+    P.hi = ctx->cells.hi;
+    P.diam = ctx->cells.diam;
+    P.d = ctx->d;
+    P.inf = std::isinf(ctx->tau_factor) ? 1 : 0;
+    P.c = P.inf ? 0.0 : ctx->tau_factor;
+    Panels& pan = ctx->pan;
+    mlb::Arena& A = ctx->arena_asm;
+    pan.ncols = (int*)dalloc(ctx, A, sizeof(int) * ncell);
+    int* nblk = (int*)dalloc(ctx, A, sizeof(int) * ncell);
+    pan.valOff = (int64_t*)dalloc(ctx, A, sizeof(int64_t) * ncell);
+    pan.colOff = (int64_t*)dalloc(ctx, A, sizeof(int64_t) * ncell);
+    pan.bcol = (int*)dalloc(ctx, A, sizeof(int) * (size_t)ncell * ncell);
+    int* colOrder = (int*)dalloc(ctx, A, sizeof(int) * ncell);
+    if (!pan.ncols || !nblk || !pan.valOff || !pan.colOff || !pan.bcol || !colOrder) return MLB_ENOMEM;
+    const unsigned wb = (unsigned)((ncell * 32 + 255) / 256);
+    count_kernel<<<wb, 256, 0, st>>>(P, ctx->cells, ncell, pan.ncols, nblk);
+    MLB_CHECK_LAUNCH(ctx, "count_kernel");
+    std::vector<int> hn(ncell), hb(ncell), order;
+    MLB_CUDA(ctx, cudaMemcpyAsync(hn.data(), pan.ncols, sizeof(int) * ncell, cudaMemcpyDeviceToHost, st));
+    MLB_CUDA(ctx, cudaMemcpyAsync(hb.data(), nblk, sizeof(int) * ncell, cudaMemcpyDeviceToHost, st));
+    MLB_CUDA(ctx, cudaStreamSynchronize(st));
+    std::vector<int64_t> vo(ncell), co(ncell);
+    int64_t nnz = 0, ctot = 0, blocks = 0;
+    for (int g = 0; g < ncell; ++g) {
+        vo[g] = nnz;
+        co[g] = ctot;
+        nnz += (int64_t)ctx->hcells[g].k * hn[g];
+        ctot += hn[g];
+        blocks += hb[g];
+    }
+    for (int l = t; l >= 0; --l)
+        for (int k = 0; k < (1 << l); ++k) order.push_back((1 << l) - 1 + k);
+    pan.nnz = nnz;
+    int64_t selfEntries = 0;
+    for (int g = 0; g < ncell; ++g) selfEntries += (int64_t)ctx->hcells[g].k * ctx->hcells[g].k;
+    pan.nnzUnique = (nnz + selfEntries) / 2;
+    pan.colTotal = ctot;
+    pan.blocks = blocks;
+    pan.colidx = (int*)dalloc(ctx, A, sizeof(int) * (ctot > 0 ? ctot : 1));
+    pan.vals = (double*)dalloc(ctx, A, sizeof(double) * (nnz > 0 ? nnz : 1));
+    ctx->diag = (double*)dalloc(ctx, A, sizeof(double) * ctx->nwav);
+    if (!pan.colidx || !pan.vals || !ctx->diag) return MLB_ENOMEM;
+    MLB_CUDA(ctx, cudaMemcpyAsync(pan.valOff, vo.data(), sizeof(int64_t) * ncell, cudaMemcpyHostToDevice, st));
+    MLB_CUDA(ctx, cudaMemcpyAsync(pan.colOff, co.data(), sizeof(int64_t) * ncell, cudaMemcpyHostToDevice, st));
+    MLB_CUDA(ctx, cudaMemcpyAsync(colOrder, order.data(), sizeof(int) * ncell, cudaMemcpyHostToDevice, st));
+    fill_kernel<<<wb, 256, 0, st>>>(P, ctx->cells, ncell, colOrder, pan);
+    MLB_CHECK_LAUNCH(ctx, "fill_kernel");
+
+    // per-level SS / SW matrices
+    std::vector<double*> SS(t + 1), SW(t + 1);
+    for (int l = 0; l <= t; ++l) {
+        SS[l] = (double*)dalloc(ctx, A, sizeof(double) * std::max<int64_t>(1, ctx->sumA[l] * ctx->sumA[l]));
+        SW[l] = (double*)dalloc(ctx, A, sizeof(double) * std::max<int64_t>(1, ctx->sumA[l] * ctx->sumK[l]));
+        if (!SS[l] || !SW[l]) return MLB_ENOMEM;
+    }
+    const size_t shm = sizeof(double) * (3 * kTile * kTile + 2 * kTile * kMaxDim);
+    MLB_CUDA(ctx, cudaFuncSetAttribute(galerkin_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    MLB_CUDA(ctx, cudaFuncSetAttribute(galerkin_tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    TileIn in{};
+    in.V = ctx->V;
+    in.xs = ctx->xs;
+    in.d = ctx->d;
+    in.kind = nu_kind(ctx->theta.nu);
+    in.scale = std::sqrt(2.0 * ctx->theta.nu) / ctx->theta.rho;
+    in.nugget = ctx->theta.nugget;
+    for (int l = t; l >= 0; --l) {
+        TileOut o;
+        o.SS = SS[l];
+        o.SW = SW[l];
+        o.ldSS = ctx->sumA[l];
+        o.ldSW = ctx->sumK[l];
+        o.pan = pan;
+        o.ncell = ncell;
+        const int64_t L = 1LL << l;
+        const int64_t npairs = L * (L + 1) / 2;
+        const unsigned grid = (unsigned)std::min<int64_t>(npairs, (int64_t)nsm * 16);
+        if (l == t) {
+            galerkin_tile_kernel<true><<<grid, 256, shm, st>>>(ctx->cells, l, npairs, in, o);
+        } else {
+            in.SSc = SS[l + 1];
+            in.ldSSc = ctx->sumA[l + 1];
+            galerkin_tile_kernel<false><<<grid, 256, shm, st>>>(ctx->cells, l, npairs, in, o);
+        }
+        MLB_CHECK_LAUNCH(ctx, "galerkin_tile_kernel");
+    }
+    // cross-level pass
+    int smax = 0;
+    for (auto& c : ctx->hcells) smax = std::max(smax, c.s);
+    const size_t cshm = sizeof(double) * ((size_t)smax * smax + (size_t)smax * 128);
+    MLB_CUDA(ctx, cudaFuncSetAttribute(cross_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cshm));
+    int64_t maxX = 0;
+    for (int j = t; j >= 1; --j) maxX = std::max(maxX, ctx->sumA[j - 1] * ctx->sumK[j]);
+    double* X0 = (double*)dalloc(ctx, A, sizeof(double) * std::max<int64_t>(1, maxX));
+    double* X1 = (double*)dalloc(ctx, A, sizeof(double) * std::max<int64_t>(1, maxX));
+    if (!X0 || !X1) return MLB_ENOMEM;
+    for (int j = t; j >= 1; --j) {
+        const int64_t ldX = ctx->sumK[j];
+        if (ldX == 0) continue;
+        const double* xin = SW[j];
+        double* bufs[2] = {X0, X1};
+        int which = 0;
+        for (int l = j - 1; l >= 0; --l) {
+            dim3 grid(1u << l, (unsigned)((ldX + 127) / 128));
+            cross_kernel<<<grid, 128, cshm, st>>>(ctx->cells, ctx->V, l, j, xin, bufs[which], ldX,
+                                                  ctx->levelBase[j], pan, ncell);
+            MLB_CHECK_LAUNCH(ctx, "cross_kernel");
+            xin = bufs[which];
+            which ^= 1;
+        }
+    }
+    diag_kernel<<<(unsigned)((ctx->nwav + 255) / 256), 256, 0, st>>>(ctx->cells, pan, ncell, ctx->nwav, ctx->diag);
+    MLB_CHECK_LAUNCH(ctx, "diag_kernel");
+    return MLB_OK;
+}
+
+}  // namespace mlb

@@ -1,0 +1,154 @@
+// Internal declarations of libmlblup: context layout, cell tables and the
+// kernel launchers shared between translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mlblup.h"
+
+namespace mlb {
+
+constexpr int kMaxDim = 16;       // largest point dimension d
+constexpr int kTile = 64;         // largest local basis size on the assembled path
+
+// Numbers of one cell of the kd-tree, level-order id g = 2^l - 1 + k.
+// s = size of the local basis (points for a leaf, children's scaling vectors
+// otherwise), a = scaling vectors, k = s - a wavelets.
+struct CellTables {
+    int* beg = nullptr;     // first kd position of the cell's points
+    int* end = nullptr;
+    int* s = nullptr;
+    int* a = nullptr;
+    int* k = nullptr;
+    int64_t* vOff = nullptr;   // offset of the s x s factor V in the V pool
+    int64_t* rOff = nullptr;   // offset of the a x p moment factor R in the R pool
+    int64_t* wOff = nullptr;   // first row of the cell's wavelets in W (finest level first)
+    int64_t* sOff = nullptr;   // first scaling index of the cell within its level
+    int64_t* wLoc = nullptr;   // first wavelet index of the cell within its level
+    double* lo = nullptr;      // bounding box of the cell's points (ncell x d)
+    double* hi = nullptr;
+    double* diam = nullptr;    // Euclidean diagonal of that box
+};
+
+struct HostCell {
+    int beg, end, s, a, k;
+    int64_t vOff, rOff, wOff, sOff, wLoc;
+};
+
+// Panels of the assembled C~_W: every row cell c owns a dense k_c x ncols_c
+// row-major panel holding all its blocks side by side (columns in global
+// wavelet order) and one column-index list shared by its k_c rows.
+struct Panels {
+    int64_t nnz = 0, blocks = 0, colTotal = 0, nnzUnique = 0;
+    int* ncols = nullptr;       // per cell
+    int64_t* valOff = nullptr;  // per cell, into vals
+    int64_t* colOff = nullptr;  // per cell, into colidx
+    int* colidx = nullptr;
+    int* bcol = nullptr;        // ncell x ncell: column offset of block (c, e) in panel c, or -1
+    int* rowCell = nullptr;     // per wavelet row: its cell
+    double* vals = nullptr;     // FP64 values
+    float* vals32 = nullptr;    // FP32 copy (mixed precision)
+};
+
+struct PcgState {
+    double rz, rr, bb, alpha, beta, pq;
+    int it, done, status, pad;
+};
+
+struct Arena {
+    std::vector<void*> ptrs;
+    void release();
+};
+
+}  // namespace mlb
+
+struct mlb_ctx {
+    mlb_opts opts;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int state = 0;                 // 0 empty, 1 basis, 2 assembled, 3 solved
+    int64_t launches = 0;          // kernels launched by this context
+
+    // basis
+    int64_t N = 0, nwav = 0;
+    int d = 0, p = 0, w = 0, t = 0, ncell = 0;
+    std::vector<mlb::HostCell> hcells;
+    std::vector<int64_t> sumA, sumK, levelBase, sbase;   // per level
+    std::vector<int> hperm;
+    double box_lo[mlb::kMaxDim], box_hi[mlb::kMaxDim];
+    double* xs = nullptr;          // N x d points in kd order
+    float* xs32 = nullptr;         // FP32 copy
+    int* perm = nullptr;           // kd position -> caller index
+    int* alpha = nullptr;          // p x d monomial exponents
+    double* X = nullptr;           // N x p design matrix, kd order
+    double* XtXf = nullptr;        // p x p Cholesky factor of X^T X
+    double* V = nullptr;           // pool of the cells' s x s orthogonal factors
+    double* R = nullptr;           // pool of the cells' a x p moment factors
+    double* sbuf = nullptr;        // scaling coefficients of every level (transforms)
+    int* flag = nullptr;           // device error flags
+    mlb::CellTables cells;
+    mlb::Arena arena_basis;
+
+    // assembly
+    mlb_theta theta{};
+    double tau_factor = 0;
+    mlb::Panels pan;
+    double* diag = nullptr;        // diag(C~_W)
+    double ms_assemble = 0;
+    mlb::Arena arena_asm;
+
+    // solve
+    double* gW = nullptr;          // gamma_W
+    double* gamma = nullptr;       // gamma-hat, kd order
+    double* beta = nullptr;        // beta-hat
+    double* vec = nullptr;         // PCG work vectors
+    double* partial = nullptr;
+    mlb::PcgState* pcg = nullptr;
+    mlb::Arena arena_solve;
+    mlb_info last_info{};
+};
+
+namespace mlb {
+
+// ---- error helpers -------------------------------------------------------
+mlb_status fail(mlb_ctx* ctx, mlb_status s, const std::string& msg);
+mlb_status cuda_fail(mlb_ctx* ctx, cudaError_t e, const char* where);
+void* dalloc(mlb_ctx* ctx, Arena& a, size_t bytes);
+
+#define MLB_CUDA(ctx, call)                                        \
+    do {                                                           \
+        cudaError_t e__ = (call);                                  \
+        if (e__ != cudaSuccess) return mlb::cuda_fail(ctx, e__, #call); \
+    } while (0)
+
+#define MLB_CHECK_LAUNCH(ctx, what)                                   \
+    do {                                                              \
+        (ctx)->launches += 1;                                         \
+        cudaError_t e__ = cudaGetLastError();                         \
+        if (e__ != cudaSuccess) return mlb::cuda_fail(ctx, e__, what); \
+    } while (0)
+
+// ---- launchers (defined in the .cu files) ---------------------------------
+// basis.cu
+mlb_status build_design(mlb_ctx* ctx);
+mlb_status build_factors(mlb_ctx* ctx);
+mlb_status apply_W_dev(mlb_ctx* ctx, const double* v_kd, double* out);    // N (kd) -> nwav
+mlb_status apply_Wt_dev(mlb_ctx* ctx, const double* u, double* out_kd);   // nwav -> N (kd)
+mlb_status gather_kd(mlb_ctx* ctx, const double* v_user, double* v_kd);   // caller -> kd order
+mlb_status scatter_kd(mlb_ctx* ctx, const double* v_kd, double* v_user);  // kd -> caller order
+// assemble.cu
+mlb_status assemble_dev(mlb_ctx* ctx);
+// solve.cu
+mlb_status cw_matvec_dev(mlb_ctx* ctx, const double* u, double* out);
+mlb_status solve_dev(mlb_ctx* ctx, const double* Z_kd, mlb_info* info);
+mlb_status trend_dev(mlb_ctx* ctx, const double* Z_kd);
+// ksum.cu
+mlb_status kernel_sum_dev(mlb_ctx* ctx, const double* targets, int64_t M, const double* a_kd,
+                          double* out, bool add_trend);
+
+}  // namespace mlb
