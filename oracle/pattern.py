@@ -14,17 +14,20 @@ Readings:
   (the search reaches every such cell, since a cell's points lie inside its kd
   region; its result is filtered by this box test).  The test is symmetric in
   the two cells, so the pattern of C~_W is symmetric.
-* tau_{i,j}: the configurations state "tau = c cell diameters".  For a source
-  cell m and target cell q, tau_{mq} = c * sqrt(D_m * D_q) with D the Euclidean
-  diagonal of the cell's point bounding box -- the geometric mean mirrors the
-  paper's level-pair form tau_{ij} = 2^{(t-i)/2} 2^{(t-j)/2} tau.  c = inf keeps
-  every pair (dense C_W).
+* tau_{i,j}: the paper sets one distance per level pair, tau_{i,j} =
+  2^{(t-i)/2} 2^{(t-j)/2} tau (Sec. 8.1); the configurations state "tau = c cell
+  diameters".  Here tau_{i,j} = c * sqrt(Dbar_i * Dbar_j) with Dbar_l the mean,
+  over the cells of level l, of the Euclidean diagonal of the cell's point
+  bounding box (summed cell by cell in order, then divided by the count) --
+  the geometric mean of the two levels' cell sizes in place of the paper's
+  sqrt(2^{t-i} 2^{t-j}).  c = inf keeps every pair (dense C_W).
 * Target depth j >= i (Remark after Algorithm 6: only blocks j >= i are
   computed, the rest by symmetry); all leaves sit at depth t, so the search
   always reaches depth j.
 
-Floating point: D is accumulated axis by axis in order, tau = c * sqrt(D_m D_q),
-and a pair is excluded iff on some axis lo_q - hi_m > tau or lo_m - hi_q > tau.
+Floating point: D is accumulated axis by axis in order, Dbar cell by cell in
+order, tau = c * sqrt(Dbar_i Dbar_j), and a pair is excluded iff on some axis
+lo_q - hi_m > tau or lo_m - hi_q > tau.
 """
 from __future__ import annotations
 
@@ -44,10 +47,17 @@ def diameters(tree: Tree, l: int) -> np.ndarray:
     return np.sqrt(acc)
 
 
-def tau_pair(Dm, Dq, c: float):
+def level_mean_diameter(tree: Tree, l: int) -> float:
+    acc = 0.0
+    for v in diameters(tree, l).tolist():
+        acc = acc + v
+    return acc / tree.ncells(l)
+
+
+def tau_levels(tree: Tree, i: int, j: int, c: float) -> float:
     if math.isinf(c):
-        return np.full(np.broadcast(Dm, Dq).shape, np.inf)
-    return c * np.sqrt(Dm * Dq)
+        return math.inf
+    return c * math.sqrt(level_mean_diameter(tree, i) * level_mean_diameter(tree, j))
 
 
 def box_admissible(lo_m, hi_m, lo_q, hi_q, tau) -> np.ndarray:
@@ -61,8 +71,7 @@ def box_admissible(lo_m, hi_m, lo_q, hi_q, tau) -> np.ndarray:
 
 def level_pair_bruteforce(tree: Tree, i: int, j: int, c: float) -> np.ndarray:
     """Boolean (2^i, 2^j) matrix of admissible (m, q) pairs by testing all pairs."""
-    Dm, Dq = diameters(tree, i), diameters(tree, j)
-    tau = tau_pair(Dm[:, None], Dq[None, :], c)
+    tau = tau_levels(tree, i, j, c)
     return box_admissible(tree.lo[i][:, None, :], tree.hi[i][:, None, :],
                           tree.lo[j][None, :, :], tree.hi[j][None, :, :], tau)
 
@@ -92,13 +101,10 @@ def search_tree(tree: Tree, lo_K: np.ndarray, hi_K: np.ndarray, target_depth: in
 
 def level_pair_search(tree: Tree, i: int, j: int, c: float) -> np.ndarray:
     """Pattern of level pair (i, j) by Algorithms 4-6 followed by the box test."""
-    Dm, Dq = diameters(tree, i), diameters(tree, j)
-    Dq_max = Dq.max() if Dq.size else 0.0
+    tau = tau_levels(tree, i, j, c)
     out = np.zeros((tree.ncells(i), tree.ncells(j)), dtype=bool)
     for m in range(tree.ncells(i)):
-        tau_max = math.inf if math.isinf(c) else c * math.sqrt(Dm[m] * Dq_max)
-        for q in search_tree(tree, tree.lo[i][m], tree.hi[i][m], j, tau_max):
-            tau = tau_pair(Dm[m], Dq[q], c)
+        for q in search_tree(tree, tree.lo[i][m], tree.hi[i][m], j, tau):
             out[m, q] = bool(box_admissible(tree.lo[i][m], tree.hi[i][m],
                                             tree.lo[j][q], tree.hi[j][q], tau))
     return out

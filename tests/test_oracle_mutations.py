@@ -42,8 +42,7 @@ def test_wrong_scaling_wavelet_split_is_caught(monkeypatch):
 def test_one_sided_box_test_is_caught():
     x = np.array([0.0, 0.1, 0.2, 0.3, 1.0, 1.1, 3.0, 3.1])[:, None]
     T = ot.build_tree(x, 2)
-    D = op.diameters(T, 2)
-    tau = op.tau_pair(D[:, None], D[None, :], 2.0)
+    tau = op.tau_levels(T, 2, 2, 2.0)
     lo_m, hi_m = T.lo[2][:, None, 0], T.hi[2][:, None, 0]
     lo_q, hi_q = T.lo[2][None, :, 0], T.hi[2][None, :, 0]
     bad = ~((lo_q - hi_m) > tau)                 # planted: the lo_m - hi_q side is not tested

@@ -26,30 +26,30 @@ def test_tree_search_reaches_every_box_meeting_cell():
     """The kd-region search (no box filter) returns a superset of the box test."""
     x = np.random.default_rng(7).random((500, 2))
     T = ot.build_tree(x, 16)
-    D = [op.diameters(T, l) for l in range(T.t + 1)]
     for i in range(T.t + 1):
         for j in range(i, T.t + 1):
             brute = op.level_pair_bruteforce(T, i, j, 1.0)
+            tau = op.tau_levels(T, i, j, 1.0)
             for m in range(T.ncells(i)):
-                tau = 1.0 * math.sqrt(D[i][m] * D[j].max())
                 found = set(op.search_tree(T, T.lo[i][m], T.hi[i][m], j, tau))
                 assert set(np.nonzero(brute[m])[0]) <= found
 
 
 def test_hand_example_one_dimension():
     """Eight points on a line, leaves of 2: cells {0,1},{2,3},{4,5},{6,7} at
-    positions 0, .1 | .2, .3 | 1, 1.1 | 3, 3.1.  Diameters 0.1 each; with
-    c = 2, tau = 0.2, so leaf 0 meets leaf 1 (gap 0.1) but not leaf 2 (gap 0.7)."""
+    positions 0, .1 | .2, .3 | 1, 1.1 | 3, 3.1.  Leaf diameters 0.1, mean 0.1;
+    with c = 2, tau_22 = 0.2, so leaf 0 meets leaf 1 (gap 0.1) but not leaf 2
+    (gap 0.7).  Level-1 cells [0, .3] and [1, 3.1] have diameters .3 and 2.1,
+    mean 1.2, so tau_11 = 2.4 and tau_12 = 2 sqrt(1.2 * 0.1) = 0.6928."""
     x = np.array([0.0, 0.1, 0.2, 0.3, 1.0, 1.1, 3.0, 3.1])[:, None]
     T = ot.build_tree(x, 2)
     assert T.t == 2
     adm = op.level_pair_bruteforce(T, 2, 2, 2.0)
     expect = np.array([[1, 1, 0, 0], [1, 1, 0, 0], [0, 0, 1, 0], [0, 0, 0, 1]], bool)
     assert np.array_equal(adm, expect)
-    # level 1 cells: [0, .3] (D=.3) and [1, 3.1] (D=2.1): tau = 2 sqrt(.63) = 1.587 > gap .7
-    assert op.level_pair_bruteforce(T, 1, 1, 2.0).all()
-    # cross level, level-1 cell [0, .3] (D .3) vs leaves (D .1): tau = 2 sqrt(.03) = .346,
-    # so leaf [1, 1.1] (gap .7) and leaf [3, 3.1] are out; level-1 cell [1, 3.1]
-    # (D 2.1): tau = 2 sqrt(.21) = .917 >= gap .9 to leaf [0, .1], so every leaf is in.
+    assert op.level_pair_bruteforce(T, 1, 1, 2.0).all()            # gap .7 < 2.4
+    # cross level: [0, .3] misses [1, 1.1] (gap .7 > .6928) and [3, 3.1];
+    # [1, 3.1] misses [0, .1] (gap .9) and [.2, .3] (gap .7)
     cross = op.level_pair_bruteforce(T, 1, 2, 2.0)
-    assert np.array_equal(cross, np.array([[1, 1, 0, 0], [1, 1, 1, 1]], bool))
+    assert np.array_equal(cross, np.array([[1, 1, 0, 0], [0, 0, 1, 1]], bool))
+    assert abs(op.tau_levels(T, 1, 2, 2.0) - 2 * math.sqrt(1.2 * 0.1)) < 1e-15
