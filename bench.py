@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the multilevel BLUP hot path on one GB300 (or N replicas).
+
+One step = one BLUP solve from scratch on the resident inputs: kd-tree and
+multilevel basis, assembly of C~_W, diagonal PCG, gamma = W^T gamma_W, the
+trend step and the prediction at the targets (every row of the hot path).
+
+Workload (default): n = 32,768 points uniform in [0,1]^5, Matern nu = 3/2,
+rho = 0.3, nugget 1e-4, w = 1 (p = 6), leaf size 64, tau = inf (the full
+C_W, 1.07e9 entries), PCG tol 1e-10, 4,096 held-out targets.  Synthetic,
+seeded.  `--workload config2` (n = 65,536 in [0,1]^3 with 8 tight clusters,
+nugget 1e-6, tau = 2 diameters) and `config3` are available too.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "BLUP solves/s & C_W entries/s, mixed vs FP64 GPU at 1e-5 rel err; % roofline"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--single", action="store_true", help="measure only --precision")
+    ap.add_argument("--workload", default="config5", choices=["config5", "config2", "config3"])
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--targets", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks -----
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.th.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- helpers -----
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            j = json.load(f)
+        return j.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of the kernel's file."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        j = json.load(f).get(kernel)
+    if not j:
+        return None
+    src = os.path.join(ROOT, "paper_1701_00285_gb300", "csrc", j["file"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return j["bytes_per_launch"] if sha == j["sha"] else None
+
+
+def workload(args, rank=0):
+    import workloads as wl
+    kw = {}
+    if args.n:
+        kw["N"] = args.n
+    if args.targets:
+        kw["M"] = args.targets
+    return getattr(wl, args.workload)(**kw)
+
+
+def describe(P) -> str:
+    tau = "inf (full C_W)" if math.isinf(P.tau_factor) else f"{P.tau_factor:g} cell diameters"
+    return (f"{P.name}: multilevel BLUP, n={P.N}, d={P.d}, Matern nu={P.nu:g} rho={P.rho:g} "
+            f"nugget={P.nugget:g}, w={P.w} (p={math.comb(P.d + P.w, P.w)}), leaf {P.leaf_size}, "
+            f"tau={tau}, PCG tol {P.pcg_rtol:g}, {P.targets.shape[0]} targets")
+
+
+def _oracle_sample(name: str, sample_n: int, sample_m: int, n: int, m: int) -> float:
+    """Seconds the oracle takes for one multilevel BLUP on the subsample."""
+    import workloads as wl
+    from oracle import mlblup
+    P = getattr(wl, name)(N=n, M=m)
+    S = wl.subsample(P, sample_n, seed=1, m=sample_m)
+    t0 = time.perf_counter()
+    mlblup.blup(S.points, S.Z, S.targets, S.w, S.nu, S.rho, S.nugget, S.leaf_size,
+                tau_factor=S.tau_factor, rtol=S.pcg_rtol, maxit=20000)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(P, sample_n=2048, sample_m=512):
+    """The oracle as it stands (numpy FP64: Alg. 7 assembly, PCG, trend step,
+    prediction) on a seeded subsample of the same workload, in a fresh
+    single-threaded process, extrapolated to the full size by the N^2 cost of
+    kernel evaluation."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import bench, sys; print(bench._oracle_sample(%r, %d, %d, %d, %d))"
+            % (P.name.split("_")[0], sample_n, sample_m, P.N, P.targets.shape[0]))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    dt = float(r.stdout.strip().splitlines()[-1])
+    scale = (P.N / sample_n) ** 2
+    return {"value": 1.0 / (dt * scale), "unit": "BLUP solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle multilevel BLUP (Alg. 7 assembly, PCG, trend, prediction) on a seeded "
+                      f"{sample_n}-point subsample with {sample_m} targets, one thread: {dt:.2f} s; "
+                      f"scaled to N={P.N} by (N/{sample_n})^2 = {scale:.0f}x",
+            "sample_seconds": dt}
+
+
+# ------------------------------------------------------------ reference -----
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    P = workload(args)
+    for _ in range(max(0, args.warmup)):
+        cpu_baseline(P, sample_n=256, sample_m=64)
+    vals = []
+    t_total = 0.0
+    for _ in range(args.steps):
+        cb = cpu_baseline(P, sample_n=1024, sample_m=256)
+        vals.append(cb["value"])
+        t_total += cb["sample_seconds"]
+    value = args.steps / sum(1.0 / v for v in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "BLUP solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": describe(P), "cache": "oracle on host cores"},
+            "cpu_baseline": {"value": value, "unit": "BLUP solves/s", "cores": 1,
+                             "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": "BLUP solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours -----
+def measure(pkg, torch, P, precision, args, dev, local_rank, world, stream):
+    """Warm-up, then K timed steps of one precision on the resident inputs."""
+    N, d, M, p = P.N, P.d, P.targets.shape[0], math.comb(P.d + P.w, P.w)
+    ctx = pkg.Context(precision, leaf_size=P.leaf_size, pcg_rtol=P.pcg_rtol, pcg_maxit=50000,
+                      device=local_rank)
+    ctx.set_stream(stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        pts = torch.from_numpy(P.points).to(dev)
+        Z = torch.from_numpy(P.Z).to(dev)
+        tg = torch.from_numpy(P.targets).to(dev)
+        yhat = torch.empty(M, dtype=torch.float64, device=dev)
+        beta = torch.empty(p, dtype=torch.float64, device=dev)
+    stream.synchronize()
+    infos = []
+
+    def step():
+        ctx.build_basis_dev(pts.data_ptr(), N, d, P.w)
+        ctx.assemble(P.nu, P.rho, P.nugget, P.tau_factor)
+        infos.append(ctx.solve_dev(Z.data_ptr(), beta.data_ptr()))
+        ctx.predict_dev(tg.data_ptr(), M, yhat.data_ptr())
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    infos.clear()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.launch_count()
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        e1.synchronize()
+    launches = ctx.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    info = infos[-1]
+    out = {"ctx": ctx, "ms": ms, "ms_step": ms / args.steps, "value": world * args.steps / (ms / 1000.0),
+           "info": info, "launches": launches, "clocks": clk.summary(),
+           "yhat": yhat.cpu().numpy(), "beta": beta.cpu().numpy()}
+
+    # the PCG matrix-vector product alone, timed live on its stream
+    nwav = N - p
+    with torch.cuda.stream(stream):
+        u = torch.randn(nwav, dtype=torch.float64, device=dev)
+        o = torch.empty(nwav, dtype=torch.float64, device=dev)
+    stream.synchronize()
+    reps = 20
+    for _ in range(3):
+        ctx.cw_matvec_dev(u.data_ptr(), o.data_ptr())
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(reps):
+        ctx.cw_matvec_dev(u.data_ptr(), o.data_ptr())
+    s1.record(stream)
+    s1.synchronize()
+    out["spmv_ms"] = s0.elapsed_time(s1) / reps
+    vb = 4 if precision == "mixed" else 8
+    # algorithmic bytes of one product: every stored value once, each panel's
+    # column list once, x read and y written once
+    out["spmv_bytes"] = info["nnz"] * vb + info["col_total"] * 4 + 2 * nwav * 8
+    return out
+
+
+def e2e_run(ctx, P, args, world, torch):
+    hp, hz, ht = P.points.copy(), P.Z.copy(), P.targets.copy()
+    ctx.set_stream(None)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.build_basis(hp, P.w)
+        ctx.assemble(P.nu, P.rho, P.nugget, P.tau_factor)
+        hb, _ = ctx.solve(hz)
+        hy = ctx.predict(ht)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": world * args.steps / dt, "unit": "BLUP solves/s",
+            "h2d_bytes_per_step": int(hp.nbytes + hz.nbytes + ht.nbytes),
+            "d2h_bytes_per_step": int(hy.nbytes + hb.nbytes)}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1701_00285_gb300 as pkg
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    P = workload(args, rank)
+    stream = torch.cuda.Stream(device=dev)
+    head = measure(pkg, torch, P, args.precision, args, dev, local_rank, world, stream)
+    other_prec = "fp64" if args.precision == "mixed" else "mixed"
+    other = None if args.single else measure(pkg, torch, P, other_prec, args, dev, local_rank, world, stream)
+    e2e = None if args.no_e2e else e2e_run(head["ctx"], P, args, world, torch)
+    info = head["info"]
+    peak, peak_kind = peaks()
+    achieved = head["spmv_bytes"] / (head["spmv_ms"] / 1000.0) / 1e9
+    kname = "spmv_panel_kernel<float>" if args.precision == "mixed" else "spmv_panel_kernel<double>"
+    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind, "traffic": recorded_traffic(kname),
+            "algorithmic_bytes": head["spmv_bytes"], "ms_per_launch": head["spmv_ms"]}
+    line = {"metric": METRIC, "value": head["value"], "unit": "BLUP solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": describe(P), "precision": args.precision,
+                       "parallelism": f"replicas{world}",
+                       "cache": "working set (C~_W %.1f GB) larger than L2" % (info["nnz"] * 8 / 1e9)},
+            "cw_entries_per_s": info["nnz_unique"] / (info["ms_assemble"] / 1000.0) if info["ms_assemble"] else None,
+            "phases_ms": {"assemble": info["ms_assemble"], "pcg": info["ms_pcg"], "trend": info["ms_beta"]},
+            "pcg_iterations": info["iterations"], "nnz": info["nnz"], "nnz_unique": info["nnz_unique"],
+            "roofline": roof, "e2e": e2e, "gpu_launches": head["launches"], "clocks": head["clocks"]}
+    if other is not None:
+        oi = other["info"]
+        ref, got = (other, head) if args.precision == "mixed" else (head, other)
+        line[other_prec] = {"value": other["value"], "ms_per_step": other["ms_step"],
+                            "phases_ms": {"assemble": oi["ms_assemble"], "pcg": oi["ms_pcg"], "trend": oi["ms_beta"]},
+                            "pcg_iterations": oi["iterations"],
+                            "cw_entries_per_s": oi["nnz_unique"] / (oi["ms_assemble"] / 1000.0) if oi["ms_assemble"] else None,
+                            "spmv_ms": other.get("spmv_ms"), "clocks": other["clocks"]}
+        line["mixed_vs_fp64"] = {
+            "rel_pred_err": float(np.linalg.norm(got["yhat"] - ref["yhat"]) / np.linalg.norm(ref["yhat"])),
+            "rel_beta_err": float(np.linalg.norm(got["beta"] - ref["beta"]) / np.linalg.norm(ref["beta"])),
+            "speedup": (head["value"] / other["value"]) if args.precision == "mixed" else (other["value"] / head["value"])}
+        other["ctx"].close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(P).items() if k != "sample_seconds"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    head["ctx"].close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -91,6 +91,7 @@ typedef struct {
     double ms_beta;            /* device time of gamma = W^T g and the beta step */
     int64_t nnz_unique;        /* entries of the blocks j >= i (each symmetric pair once) */
     int64_t launches;          /* kernels this context has launched since mlb_create */
+    int64_t col_total;         /* column indices stored (one list per row panel) */
 } mlb_info;
 
 /* Fills *opts with defaults: FP64, n0 = 64, rtol 1e-10, maxit 20000, diagonal
@@ -121,10 +122,11 @@ mlb_status mlb_build_basis(mlb_ctx* ctx, const double* points, int64_t N, int d,
 /* Same with points in device memory. */
 mlb_status mlb_build_basis_dev(mlb_ctx* ctx, const double* points_dev, int64_t N, int d, int w);
 
-/* Sparse multilevel covariance C~_W (Sec. 4, Algs. 4-7) for theta.  A cell
- * pair (m, q) is kept when the bounding box of q's points meets the box of
- * m's points grown by tau_mq = tau_factor * sqrt(D_m D_q) on every axis (D =
- * box diagonal); tau_factor = INFINITY keeps every pair.  Also forms
+/* Sparse multilevel covariance C~_W (Sec. 4, Algs. 4-7) for theta.  A pair of
+ * cells (m of level i, q of level j) is kept when the bounding box of q's
+ * points meets the box of m's points grown on every axis by
+ * tau_ij = tau_factor * sqrt(Dbar_i Dbar_j), Dbar_l the mean box diagonal of
+ * the cells of level l; tau_factor = INFINITY keeps every pair.  Also forms
  * P_W = diag(C~_W).  With opts.matrix_free = 1 only theta is recorded (tau_factor
  * must be INFINITY).  MLB_EINVAL: bad theta, leaf_size or 2p above 64 on the
  * assembled path. */

@@ -42,7 +42,7 @@ class Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("nnz", ctypes.c_int64), ("blocks", ctypes.c_int64), ("ms_assemble", ctypes.c_double),
                 ("ms_pcg", ctypes.c_double), ("ms_beta", ctypes.c_double),
-                ("nnz_unique", ctypes.c_int64), ("launches", ctypes.c_int64)]
+                ("nnz_unique", ctypes.c_int64), ("launches", ctypes.c_int64), ("col_total", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

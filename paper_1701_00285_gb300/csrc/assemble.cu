@@ -28,6 +28,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "ff.cuh"
 #include "matern.cuh"
 
 namespace mlb {
@@ -41,8 +42,10 @@ struct PatArgs {
     double c;
 };
 
-// Distance criterion: the box of q meets the box of m grown by
-// tau = c sqrt(D_m D_q) on every axis (symmetric in m and q).
+// Distance criterion (Sec. 4.1): the box of q's points meets the box of m's
+// points grown by tau_{i,j} = c sqrt(Dbar_i Dbar_j) on every axis, Dbar_l the
+// mean box diagonal of level l (the cell tables carry it per cell).  The test
+// is symmetric in m and q.
 __device__ __forceinline__ bool admissible(const PatArgs& P, int gm, int gq) {
     if (P.inf) return true;
     const double tau = __dmul_rn(P.c, sqrt(__dmul_rn(P.diam[gm], P.diam[gq])));
@@ -126,6 +129,9 @@ struct TileIn {
     const double* V;     // pool of the cells' orthogonal factors
     // leaf pass: kernel block on the fly
     const double* xs;
+    const float* xl32;   // mixed: offsets of the points from their leaf's centre, FP32 high part
+    const float* xl32lo; //        and low part (offset = high + low to about 1e-14)
+    const double* ctr;   // mixed: leaf centres (ncell x d)
     int d, kind;
     double scale, nugget;
     // level pass: children's SS matrix
@@ -167,14 +173,14 @@ __device__ __forceinline__ void put_entry(const CellTables& C, const TileOut& o,
 }
 
 // G = V_f^T H V_e for every pair f <= e of one level (tiles up to 64 x 64,
-// 256 threads, 4 x 4 register micro-tiles).  H is the covariance block of the
-// two leaves (LEAF) or the children's SS blocks (coarser levels).
+// 256 threads, 4 x 4 register micro-tiles), FP64.  H is the covariance block
+// of the two leaves (LEAF) or the children's SS blocks (coarser levels).
 template <bool LEAF>
 __global__ void __launch_bounds__(256) galerkin_tile_kernel(CellTables C, int level, int64_t npairs,
                                                             TileIn in, TileOut out) {
     constexpr int S = kTile;
-    extern __shared__ double sm[];
-    double* Vf = sm;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* Vf = reinterpret_cast<double*>(smraw);
     double* Ve = Vf + S * S;
     double* P = Ve + S * S;
     double* xf = P + S * S;
@@ -202,7 +208,6 @@ __global__ void __launch_bounds__(256) galerkin_tile_kernel(CellTables C, int le
             for (int idx = tid; idx < se * d; idx += 256) xe[idx] = in.xs[be * d + idx];
         }
         __syncthreads();
-        // H
         if (LEAF) {
             const int d = in.d;
             for (int idx = tid; idx < S * S; idx += 256) {
@@ -227,7 +232,6 @@ __global__ void __launch_bounds__(256) galerkin_tile_kernel(CellTables C, int le
             }
         }
         __syncthreads();
-        // T = H V_e
         double acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -250,7 +254,6 @@ __global__ void __launch_bounds__(256) galerkin_tile_kernel(CellTables C, int le
 #pragma unroll
             for (int j = 0; j < 4; ++j) P[(r0 + i) * S + c0 + j] = acc[i][j];
         __syncthreads();
-        // G = V_f^T T
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -276,6 +279,175 @@ __global__ void __launch_bounds__(256) galerkin_tile_kernel(CellTables C, int le
             }
         __syncthreads();
     }
+}
+
+// Mixed leaf pass: G = V_f^T Phi V_e on the FP32 pipes.  Phi is evaluated in
+// double-float (ff.cuh): coordinates as double-float offsets from the leaf
+// centres plus the double-float difference of the two centres, distance,
+// square root, exponential and polynomial in double-float.  Both contractions
+// run on split operands (Phi = Phi_hi + Phi_lo, V = V_hi + V_lo, T = T_hi +
+// T_lo): the leading products in a cascaded FP32 sum (Sum2), their rounding
+// errors (Dekker's TwoProduct, one FMA each) and the cross terms in plain FP32
+// sums.  Rounding V or Phi to one FP32 number would perturb the
+// wavelet entries at the 1e-7 level of the smooth part of Phi, which the
+// vanishing moments otherwise cancel.  The nugget is added in FP64 to G's
+// diagonal (V is orthogonal).
+__global__ void __launch_bounds__(256) galerkin_leaf_f32_kernel(CellTables C, int level, int64_t npairs,
+                                                                TileIn in, TileOut out) {
+    constexpr int S = kTile;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float* Vfh = reinterpret_cast<float*>(smraw);
+    float* Vfl = Vfh + S * S;
+    float* Veh = Vfl + S * S;
+    float* Vel = Veh + S * S;
+    float* P = Vel + S * S;       // Phi_hi, then T_hi
+    float* Pl = P + S * S;        // Phi_lo, then T_lo
+    // the coordinates live in the V buffers until Phi is formed
+    float* xfh = Vfh;
+    float* xfl = Vfh + S * kMaxDim;
+    float* xeh = Veh;
+    float* xel = Veh + S * kMaxDim;
+    __shared__ float dch[kMaxDim], dcl[kMaxDim];
+    __shared__ float2 tab[64];
+    ff_fill_exp2_table(tab);
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+    const int r0 = ty * 4, c0 = tx * 4;
+    const int first = (1 << level) - 1;
+    const ff scale = ff_from_double(in.scale);
+    for (int64_t pi = blockIdx.x; pi < npairs; pi += gridDim.x) {
+        int f, e;
+        unrank_pair(pi, f, e);
+        const int gf = first + f, ge = first + e;
+        const int sf = C.s[gf], se = C.s[ge], af = C.a[gf], ae = C.a[ge];
+        const int d = in.d;
+        const int64_t bf = C.beg[gf], be = C.beg[ge];
+        for (int idx = tid; idx < sf * d; idx += 256) {
+            xfh[idx] = in.xl32[bf * d + idx];
+            xfl[idx] = in.xl32lo[bf * d + idx];
+        }
+        for (int idx = tid; idx < se * d; idx += 256) {
+            xeh[idx] = in.xl32[be * d + idx];
+            xel[idx] = in.xl32lo[be * d + idx];
+        }
+        if (tid < d) {
+            const ff dc = ff_from_double(in.ctr[gf * d + tid] - in.ctr[ge * d + tid]);
+            dch[tid] = dc.h;
+            dcl[tid] = dc.l;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < S * S; idx += 256) {
+            const int r = idx / S, c = idx % S;
+            ff v = {0.0f, 0.0f};
+            if (r < sf && c < se) {
+                ff r2 = {0.0f, 0.0f};
+                for (int k = 0; k < d; ++k) {
+                    ff df = ff_two_sum(xfh[r * d + k], -xeh[c * d + k]);
+                    df = ff_add(df, {__fsub_rn(xfl[r * d + k], xel[c * d + k]), 0.0f});
+                    df = ff_add(df, {dch[k], dcl[k]});
+                    r2 = ff_add(r2, ff_mul(df, df));
+                }
+                v = ff_matern(ff_sqrt(r2), in.kind, scale, tab);
+            }
+            P[idx] = v.h;
+            Pl[idx] = v.l;
+        }
+        __syncthreads();
+        const double* gVf = in.V + C.vOff[gf];
+        const double* gVe = in.V + C.vOff[ge];
+        for (int idx = tid; idx < S * S; idx += 256) {
+            const int r = idx / S, c = idx % S;
+            const double vf = (r < sf && c < sf) ? gVf[r * sf + c] : 0.0;
+            const double ve = (r < se && c < se) ? gVe[r * se + c] : 0.0;
+            const float vfh = (float)vf, veh = (float)ve;
+            Vfh[idx] = vfh;
+            Vfl[idx] = (float)(vf - (double)vfh);
+            Veh[idx] = veh;
+            Vel[idx] = (float)(ve - (double)veh);
+        }
+        __syncthreads();
+        // T = (Phi_hi + Phi_lo)(V_hi + V_lo)
+        float ah[4][4], ac[4][4], al[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ah[i][j] = ac[i][j] = al[i][j] = 0.0f;
+        for (int k = 0; k < S; ++k) {
+            float a4[4], a4l[4], bh[4], bl[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a4[i] = P[(r0 + i) * S + k];
+                a4l[i] = Pl[(r0 + i) * S + k];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                bh[j] = Veh[k * S + c0 + j];
+                bl[j] = Vel[k * S + c0 + j];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float pr = __fmul_rn(a4[i], bh[j]);
+                    sum2_add(ah[i][j], ac[i][j], pr);
+                    // rounding error of the product (TwoProduct) and the cross terms
+                    al[i][j] = fmaf(a4[i], bl[j], fmaf(a4l[i], bh[j], __fadd_rn(al[i][j], fmaf(a4[i], bh[j], -pr))));
+                }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                P[(r0 + i) * S + c0 + j] = ah[i][j];
+                Pl[(r0 + i) * S + c0 + j] = __fadd_rn(al[i][j], ac[i][j]);
+            }
+        __syncthreads();
+        // G = (V_hi + V_lo)^T (T_hi + T_lo)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ah[i][j] = ac[i][j] = al[i][j] = 0.0f;
+        for (int k = 0; k < S; ++k) {
+            float uh[4], ul[4], th[4], tl[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uh[i] = Vfh[k * S + r0 + i];
+                ul[i] = Vfl[k * S + r0 + i];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                th[j] = P[k * S + c0 + j];
+                tl[j] = Pl[k * S + c0 + j];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float pr = __fmul_rn(uh[i], th[j]);
+                    sum2_add(ah[i][j], ac[i][j], pr);
+                    al[i][j] = fmaf(uh[i], tl[j], fmaf(ul[i], th[j], __fadd_rn(al[i][j], fmaf(uh[i], th[j], -pr))));
+                }
+        }
+        const bool diagPair = (gf == ge);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = r0 + i, c = c0 + j;
+                if (r < sf && c < se) {
+                    double v = (double)ah[i][j] + ((double)al[i][j] + (double)ac[i][j]);
+                    if (diagPair && r == c) v += in.nugget;
+                    put_entry(C, out, gf, ge, diagPair, af, ae, r, c, v);
+                }
+            }
+        __syncthreads();
+    }
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ src, int64_t n, float* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
 }
 
 // One step of the cross-level pass: rows of X_{l+1} (scaling functions of
@@ -351,13 +523,18 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
     MLB_CUDA(ctx, cudaMemcpyAsync(hn.data(), pan.ncols, sizeof(int) * ncell, cudaMemcpyDeviceToHost, st));
     MLB_CUDA(ctx, cudaMemcpyAsync(hb.data(), nblk, sizeof(int) * ncell, cudaMemcpyDeviceToHost, st));
     MLB_CUDA(ctx, cudaStreamSynchronize(st));
+    // panels padded to a width that is a multiple of 4 (zero values, column 0)
+    // so that every row starts 16-byte aligned for the vector loads of the SpMV
     std::vector<int64_t> vo(ncell), co(ncell);
-    int64_t nnz = 0, ctot = 0, blocks = 0;
+    std::vector<int> padded(ncell);
+    int64_t nnz = 0, stored = 0, ctot = 0, blocks = 0;
     for (int g = 0; g < ncell; ++g) {
-        vo[g] = nnz;
+        padded[g] = ctx->hcells[g].k > 0 ? (hn[g] + 3) & ~3 : 0;
+        vo[g] = stored;
         co[g] = ctot;
         nnz += (int64_t)ctx->hcells[g].k * hn[g];
-        ctot += hn[g];
+        stored += (int64_t)ctx->hcells[g].k * padded[g];
+        ctot += padded[g];
         blocks += hb[g];
     }
     for (int l = t; l >= 0; --l)
@@ -368,10 +545,14 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
     pan.nnzUnique = (nnz + selfEntries) / 2;
     pan.colTotal = ctot;
     pan.blocks = blocks;
+    pan.stored = stored;
     pan.colidx = (int*)dalloc(ctx, A, sizeof(int) * (ctot > 0 ? ctot : 1));
-    pan.vals = (double*)dalloc(ctx, A, sizeof(double) * (nnz > 0 ? nnz : 1));
+    pan.vals = (double*)dalloc(ctx, A, sizeof(double) * (stored > 0 ? stored : 1));
     ctx->diag = (double*)dalloc(ctx, A, sizeof(double) * ctx->nwav);
     if (!pan.colidx || !pan.vals || !ctx->diag) return MLB_ENOMEM;
+    MLB_CUDA(ctx, cudaMemsetAsync(pan.colidx, 0, sizeof(int) * (ctot > 0 ? ctot : 1), st));
+    MLB_CUDA(ctx, cudaMemsetAsync(pan.vals, 0, sizeof(double) * (stored > 0 ? stored : 1), st));
+    MLB_CUDA(ctx, cudaMemcpyAsync(pan.ncols, padded.data(), sizeof(int) * ncell, cudaMemcpyHostToDevice, st));
     MLB_CUDA(ctx, cudaMemcpyAsync(pan.valOff, vo.data(), sizeof(int64_t) * ncell, cudaMemcpyHostToDevice, st));
     MLB_CUDA(ctx, cudaMemcpyAsync(pan.colOff, co.data(), sizeof(int64_t) * ncell, cudaMemcpyHostToDevice, st));
     MLB_CUDA(ctx, cudaMemcpyAsync(colOrder, order.data(), sizeof(int) * ncell, cudaMemcpyHostToDevice, st));
@@ -385,15 +566,21 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
         SW[l] = (double*)dalloc(ctx, A, sizeof(double) * std::max<int64_t>(1, ctx->sumA[l] * ctx->sumK[l]));
         if (!SS[l] || !SW[l]) return MLB_ENOMEM;
     }
+    const bool mixed = ctx->opts.precision == MLB_MIXED;
     const size_t shm = sizeof(double) * (3 * kTile * kTile + 2 * kTile * kMaxDim);
+    const size_t shm32 = sizeof(float) * (6 * kTile * kTile);
     MLB_CUDA(ctx, cudaFuncSetAttribute(galerkin_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     MLB_CUDA(ctx, cudaFuncSetAttribute(galerkin_tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    MLB_CUDA(ctx, cudaFuncSetAttribute(galerkin_leaf_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm32));
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     TileIn in{};
     in.V = ctx->V;
     in.xs = ctx->xs;
+    in.xl32 = ctx->xl32;
+    in.xl32lo = ctx->xl32lo;
+    in.ctr = ctx->leafctr;
     in.d = ctx->d;
     in.kind = nu_kind(ctx->theta.nu);
     in.scale = std::sqrt(2.0 * ctx->theta.nu) / ctx->theta.rho;
@@ -410,7 +597,12 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
         const int64_t npairs = L * (L + 1) / 2;
         const unsigned grid = (unsigned)std::min<int64_t>(npairs, (int64_t)nsm * 16);
         if (l == t) {
-            galerkin_tile_kernel<true><<<grid, 256, shm, st>>>(ctx->cells, l, npairs, in, o);
+            if (mixed) {
+                const unsigned g32 = (unsigned)std::min<int64_t>(npairs, (int64_t)nsm * 32);
+                galerkin_leaf_f32_kernel<<<g32, 256, shm32, st>>>(ctx->cells, l, npairs, in, o);
+            } else {
+                galerkin_tile_kernel<true><<<grid, 256, shm, st>>>(ctx->cells, l, npairs, in, o);
+            }
         } else {
             in.SSc = SS[l + 1];
             in.ldSSc = ctx->sumA[l + 1];
@@ -445,6 +637,23 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
     }
     diag_kernel<<<(unsigned)((ctx->nwav + 255) / 256), 256, 0, st>>>(ctx->cells, pan, ncell, ctx->nwav, ctx->diag);
     MLB_CHECK_LAUNCH(ctx, "diag_kernel");
+    // the SS / SW work matrices are no longer needed
+    for (int l = 0; l <= t; ++l) {
+        dfree(A, SS[l]);
+        dfree(A, SW[l]);
+    }
+    dfree(A, X0);
+    dfree(A, X1);
+    if (mixed) {
+        // the mixed path keeps C~_W in FP32: half the bytes per product
+        pan.vals32 = (float*)dalloc(ctx, A, sizeof(float) * std::max<int64_t>(1, stored));
+        if (!pan.vals32) return MLB_ENOMEM;
+        to_f32_kernel<<<1216, 256, 0, st>>>(pan.vals, std::max<int64_t>(1, stored), pan.vals32);
+        MLB_CHECK_LAUNCH(ctx, "to_f32_kernel");
+        MLB_CUDA(ctx, cudaStreamSynchronize(st));
+        dfree(A, pan.vals);
+        pan.vals = nullptr;
+    }
     return MLB_OK;
 }
 

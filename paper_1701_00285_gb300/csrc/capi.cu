@@ -29,6 +29,16 @@ mlb_status cuda_fail(mlb_ctx* ctx, cudaError_t e, const char* where) {
                 std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+void dfree(Arena& a, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < a.ptrs.size(); ++i)
+        if (a.ptrs[i] == p) {
+            cudaFree(p);
+            a.ptrs.erase(a.ptrs.begin() + i);
+            return;
+        }
+}
+
 void* dalloc(mlb_ctx* ctx, Arena& a, size_t bytes) {
     void* p = nullptr;
     if (bytes == 0) bytes = 8;
@@ -293,6 +303,11 @@ static mlb_status build_basis_host(mlb_ctx* ctx, const double* pts, int64_t N, i
     for (int64_t i = 0; i < N; ++i)
         for (int c = 0; c < d; ++c) xs[i * d + c] = pts[(int64_t)ctx->hperm[i] * d + c];
     ctx->xs = (double*)dalloc(ctx, A, sizeof(double) * N * d);
+    ctx->xs32 = (float*)dalloc(ctx, A, sizeof(float) * N * d);
+    ctx->xl32 = (float*)dalloc(ctx, A, sizeof(float) * N * d);
+    ctx->xs32lo = (float*)dalloc(ctx, A, sizeof(float) * N * d);
+    ctx->xl32lo = (float*)dalloc(ctx, A, sizeof(float) * N * d);
+    ctx->leafctr = (double*)dalloc(ctx, A, sizeof(double) * ncell * d);
     ctx->perm = (int*)dalloc(ctx, A, sizeof(int) * N);
     ctx->alpha = (int*)dalloc(ctx, A, sizeof(int) * p * d);
     ctx->X = (double*)dalloc(ctx, A, sizeof(double) * N * p);
@@ -305,8 +320,8 @@ static mlb_status build_basis_host(mlb_ctx* ctx, const double* pts, int64_t N, i
     ctx->gW = (double*)dalloc(ctx, A, sizeof(double) * ctx->nwav);
     ctx->gamma = (double*)dalloc(ctx, A, sizeof(double) * N);
     ctx->beta = (double*)dalloc(ctx, A, sizeof(double) * p);
-    ctx->vec = (double*)dalloc(ctx, A, sizeof(double) * 8 * N);
-    ctx->partial = (double*)dalloc(ctx, A, sizeof(double) * (8192 + 64 * 128));
+    ctx->vec = (double*)dalloc(ctx, A, sizeof(double) * 10 * N);
+    ctx->partial = (double*)dalloc(ctx, A, sizeof(double) * ((size_t)ncell + 16384));
     ctx->pcg = (PcgState*)dalloc(ctx, A, sizeof(PcgState));
     CellTables& C = ctx->cells;
     C.beg = (int*)dalloc(ctx, A, sizeof(int) * ncell);
@@ -323,7 +338,7 @@ static mlb_status build_basis_host(mlb_ctx* ctx, const double* pts, int64_t N, i
     C.hi = (double*)dalloc(ctx, A, sizeof(double) * ncell * d);
     C.diam = (double*)dalloc(ctx, A, sizeof(double) * ncell);
     {
-        const void* need[] = {ctx->xs, ctx->perm, ctx->alpha, ctx->X, ctx->XtXf, ctx->V, ctx->R, ctx->sbuf,
+        const void* need[] = {ctx->xs, ctx->xs32, ctx->xl32, ctx->xs32lo, ctx->xl32lo, ctx->leafctr, ctx->perm, ctx->alpha, ctx->X, ctx->XtXf, ctx->V, ctx->R, ctx->sbuf,
                               ctx->flag, ctx->pan.rowCell, ctx->gW, ctx->gamma, ctx->beta, ctx->vec,
                               ctx->partial, ctx->pcg, C.beg, C.end, C.s, C.a, C.k, C.vOff, C.rOff, C.wOff,
                               C.sOff, C.wLoc, C.lo, C.hi, C.diam};
@@ -354,8 +369,41 @@ static mlb_status build_basis_host(mlb_ctx* ctx, const double* pts, int64_t N, i
         }
         diam[g] = std::sqrt(acc);
     }
+    // tau_{i,j} = c sqrt(Dbar_i Dbar_j): every cell carries its level's mean
+    // diagonal, summed cell by cell in order
+    for (int l = 0; l <= t; ++l) {
+        double acc = 0.0;
+        const int first = (1 << l) - 1, n = 1 << l;
+        for (int k = 0; k < n; ++k) acc = acc + diam[first + k];
+        const double mean = acc / (double)n;
+        for (int k = 0; k < n; ++k) diam[first + k] = mean;
+    }
+    // FP32 coordinates of the mixed path: offsets from the data box centre, and
+    // offsets from the box centre of the point's leaf
+    std::vector<float> x32((size_t)N * d), xl((size_t)N * d), x32lo((size_t)N * d), xllo((size_t)N * d);
+    std::vector<double> ctr((size_t)ncell * d);
+    for (int g = 0; g < ncell; ++g)
+        for (int q = 0; q < d; ++q) ctr[(size_t)g * d + q] = 0.5 * (lo[(size_t)g * d + q] + hi[(size_t)g * d + q]);
+    for (int k = 0; k < (1 << t); ++k) {
+        const int g = (1 << t) - 1 + k;
+        for (int i = H[g].beg; i < H[g].end; ++i)
+            for (int q = 0; q < d; ++q) {
+                const double v = xs[(size_t)i * d + q];
+                const double og = v - 0.5 * (ctx->box_lo[q] + ctx->box_hi[q]);
+                const double ol = v - ctr[(size_t)g * d + q];
+                x32[(size_t)i * d + q] = (float)og;
+                x32lo[(size_t)i * d + q] = (float)(og - (double)(float)og);
+                xl[(size_t)i * d + q] = (float)ol;
+                xllo[(size_t)i * d + q] = (float)(ol - (double)(float)ol);
+            }
+    }
     cudaStream_t st = ctx->stream;
 #define UP(dst, src, n) MLB_CUDA(ctx, cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st))
+    UP(ctx->xs32, x32.data(), sizeof(float) * N * d);
+    UP(ctx->xl32, xl.data(), sizeof(float) * N * d);
+    UP(ctx->xs32lo, x32lo.data(), sizeof(float) * N * d);
+    UP(ctx->xl32lo, xllo.data(), sizeof(float) * N * d);
+    UP(ctx->leafctr, ctr.data(), sizeof(double) * ncell * d);
     UP(ctx->xs, xs.data(), sizeof(double) * N * d);
     UP(ctx->perm, ctx->hperm.data(), sizeof(int) * N);
     UP(ctx->alpha, ex.data(), sizeof(int) * p * d);
@@ -415,7 +463,12 @@ mlb_status mlb_assemble(mlb_ctx* ctx, const mlb_theta* th, double tau_factor) {
     cudaSetDevice(ctx->opts.device);
     cudaStreamSynchronize(ctx->stream);
     ctx->arena_asm.release();
-    ctx->pan.nnz = ctx->pan.blocks = 0;
+    {
+        int* rc = ctx->pan.rowCell;
+        ctx->pan = Panels{};
+        ctx->pan.rowCell = rc;
+        ctx->diag = nullptr;
+    }
     ctx->theta = *th;
     ctx->tau_factor = tau_factor;
     ctx->state = 1;
@@ -611,8 +664,33 @@ mlb_status mlb_kernel_sum(mlb_ctx* ctx, const double* targets, int64_t M, const 
 
 mlb_status mlb_grad(mlb_ctx* ctx, const double* targets, int64_t M, const double* y_obs, double* loss_out,
                     double* dlogrho_out, double* dlognugget_out) {
-    (void)targets; (void)M; (void)y_obs; (void)loss_out; (void)dlogrho_out; (void)dlognugget_out;
-    return fail(ctx, MLB_EINVAL, "mlb_grad is not available in this build");
+    if (!ctx || !targets || !y_obs || M < 1) return fail(ctx, MLB_EINVAL, "bad argument");
+    ctx->err.clear();
+    if (ctx->state < 3) return fail(ctx, MLB_ESTATE, "mlb_grad needs mlb_solve first");
+    cudaSetDevice(ctx->opts.device);
+    double *tg = nullptr, *y = nullptr, *o3 = nullptr;
+    mlb_status s = MLB_OK;
+    if (cudaMalloc(&tg, sizeof(double) * M * ctx->d) != cudaSuccess || cudaMalloc(&y, sizeof(double) * M) != cudaSuccess ||
+        cudaMalloc(&o3, sizeof(double) * 3) != cudaSuccess)
+        s = fail(ctx, MLB_ENOMEM, "cudaMalloc failed");
+    if (s == MLB_OK && (cudaMemcpyAsync(tg, targets, sizeof(double) * M * ctx->d, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+                        cudaMemcpyAsync(y, y_obs, sizeof(double) * M, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess))
+        s = fail(ctx, MLB_ECUDA, "copy of targets failed");
+    if (s == MLB_OK) s = grad_dev(ctx, tg, M, y, o3);
+    double h[3] = {0, 0, 0};
+    if (s == MLB_OK) {
+        cudaError_t e = cudaMemcpyAsync(h, o3, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) s = cuda_fail(ctx, e, "gradient copy");
+    }
+    cudaFree(tg);
+    cudaFree(y);
+    cudaFree(o3);
+    if (s != MLB_OK) return s;
+    if (loss_out) *loss_out = h[0];
+    if (dlogrho_out) *dlogrho_out = h[1];
+    if (dlognugget_out) *dlognugget_out = h[2];
+    return MLB_OK;
 }
 
 }  // extern "C"

@@ -43,7 +43,8 @@ struct HostCell {
 // row-major panel holding all its blocks side by side (columns in global
 // wavelet order) and one column-index list shared by its k_c rows.
 struct Panels {
-    int64_t nnz = 0, blocks = 0, colTotal = 0, nnzUnique = 0;
+    int64_t nnz = 0, blocks = 0, colTotal = 0, nnzUnique = 0, stored = 0;
+    // ncols holds the padded panel width (multiple of 4); nnz counts real entries
     int* ncols = nullptr;       // per cell
     int64_t* valOff = nullptr;  // per cell, into vals
     int64_t* colOff = nullptr;  // per cell, into colidx
@@ -82,7 +83,11 @@ struct mlb_ctx {
     std::vector<int> hperm;
     double box_lo[mlb::kMaxDim], box_hi[mlb::kMaxDim];
     double* xs = nullptr;          // N x d points in kd order
-    float* xs32 = nullptr;         // FP32 copy
+    float* xs32 = nullptr;         // mixed: FP32 offsets of the points from the data box centre
+    float* xs32lo = nullptr;       // mixed: low parts of those offsets (double-float coordinates)
+    float* xl32 = nullptr;         // mixed: FP32 offsets of the points from their leaf's box centre
+    float* xl32lo = nullptr;       // mixed: low parts of the leaf offsets
+    double* leafctr = nullptr;     // mixed: box centre of every cell (ncell x d)
     int* perm = nullptr;           // kd position -> caller index
     int* alpha = nullptr;          // p x d monomial exponents
     double* X = nullptr;           // N x p design matrix, kd order
@@ -119,6 +124,7 @@ namespace mlb {
 mlb_status fail(mlb_ctx* ctx, mlb_status s, const std::string& msg);
 mlb_status cuda_fail(mlb_ctx* ctx, cudaError_t e, const char* where);
 void* dalloc(mlb_ctx* ctx, Arena& a, size_t bytes);
+void dfree(Arena& a, void* p);
 
 #define MLB_CUDA(ctx, call)                                        \
     do {                                                           \
@@ -150,5 +156,17 @@ mlb_status trend_dev(mlb_ctx* ctx, const double* Z_kd);
 // ksum.cu
 mlb_status kernel_sum_dev(mlb_ctx* ctx, const double* targets, int64_t M, const double* a_kd,
                           double* out, bool add_trend);
+// out_k = sum_j f(|y_k - s_j|) w_j over Ns sources s (nullptr: the data points,
+// kd order); f = phi or d phi / d log(rho); optional trend k(y)^T beta.
+// On the mixed path `accurate` selects double-float kernel values (one-shot
+// sums: trend step, prediction, gradient) instead of FP32 ones (the kernel sum
+// inside every matrix-free PCG iteration).
+mlb_status kernel_sum_general(mlb_ctx* ctx, const double* targets, int64_t M, const double* sources,
+                              int64_t Ns, const double* weights, double* out, bool add_trend, bool deriv,
+                              bool accurate = true);
+// solve.cu: PCG on C~_W x = b (nwav vectors on the device)
+mlb_status pcg_run(mlb_ctx* ctx, const double* b, double* x, mlb_info* info);
+// grad.cu
+mlb_status grad_dev(mlb_ctx* ctx, const double* targets, int64_t M, const double* y, double* out3);
 
 }  // namespace mlb

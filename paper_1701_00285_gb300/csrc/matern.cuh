@@ -28,7 +28,7 @@ __device__ __forceinline__ double dmatern_dlogrho_f64(double r, int kind, double
 
 __device__ __forceinline__ float matern_f32(float r, int kind, float scale) {
     const float s = scale * r;
-    const float e = __expf(-s);
+    const float e = expf(-s);
     if (kind == 0) return e;
     if (kind == 1) return (1.0f + s) * e;
     return (1.0f + s + s * s * (1.0f / 3.0f)) * e;
@@ -36,10 +36,22 @@ __device__ __forceinline__ float matern_f32(float r, int kind, float scale) {
 
 __device__ __forceinline__ float dmatern_dlogrho_f32(float r, int kind, float scale) {
     const float s = scale * r;
-    const float e = __expf(-s);
+    const float e = expf(-s);
     if (kind == 0) return s * e;
     if (kind == 1) return s * s * e;
     return (s * s * (1.0f / 3.0f)) * (1.0f + s) * e;
+}
+
+// Cascaded FP32 accumulation (Sum2 of Ogita, Rump and Oishi, "Accurate sum and
+// dot product", 2005): every addition is an error-free TwoSum and the rounding
+// errors are summed separately, so s + e carries the sum to about twice FP32
+// precision even when the terms cancel (plain Kahan compensation does not).
+// The _rn intrinsics keep the compiler from fusing a product into the sums.
+__device__ __forceinline__ void sum2_add(float& s, float& e, float v) {
+    const float t = __fadd_rn(s, v);
+    const float bb = __fsub_rn(t, s);
+    e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(v, bb)));
+    s = t;
 }
 
 inline int nu_kind(double nu) {

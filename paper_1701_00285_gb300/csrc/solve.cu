@@ -10,14 +10,15 @@
 // chunks of iterations, which are replayed as a captured CUDA graph.
 // Stopping test: ||r_k||_2 <= rtol ||Z_W||_2 on the unpreconditioned
 // residual r_k = Z_W - C~_W g_k (remark closing Sec. 6.2).
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
+#include "matern.cuh"
 
 namespace mlb {
 
 constexpr int kVecBlocks = 512;
-constexpr int kSpmvBlocks = 1216;   // 8 x 152 SMs, grid-stride over rows
 
 enum { ST_OK = 0, ST_BREAKDOWN = 1, ST_NOCONV = 2 };
 
@@ -36,32 +37,128 @@ __device__ double block_reduce(double v) {
     return s;   // valid in thread 0
 }
 
-// y = A x over the panels; optionally part[block] = sum_r x_r y_r.
-__global__ void __launch_bounds__(256) spmv_kernel(Panels pan, const int64_t* __restrict__ wOff, int64_t nwav,
-                                                   const double* __restrict__ x, double* __restrict__ y,
-                                                   double* __restrict__ part, const PcgState* st) {
+// y = A x over the row panels, one CTA per panel (heaviest panels first).
+// For every chunk of 256 columns the CTA stages the column indices' x values
+// once in shared memory; each warp then streams its rows' values and
+// multiplies against the staged chunk.  Only the values come from HBM.  To
+// keep enough bytes in flight every lane issues the loads of four rows times
+// four 16-byte segments before it consumes any of them (panels are padded to
+// a width that is a multiple of 4, so every row starts 16-byte aligned).
+// FP64 panels multiply in FP64 (on GB300 the FP64 pipe, not HBM, bounds this
+// product); FP32 panels multiply FP32 values by the FP32-rounded x.
+// Optionally part[block] = sum over the panel's rows of x_r y_r.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) spmv_panel_kernel(Panels pan, const T* __restrict__ vals,
+                                                         const int* __restrict__ kcell,
+                                                         const int64_t* __restrict__ wOff, int ncell,
+                                                         const double* __restrict__ x, double* __restrict__ y,
+                                                         double* __restrict__ part, const PcgState* st) {
     if (st && st->done) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    using V2 = typename Vec2<T>::type;
+    constexpr int CH = 256;
+    __shared__ T xs[CH];          // the chunk's x values, in the panel's arithmetic type
+    __shared__ T xl[CH];          // FP32 panels: the low part of x (x = x_hi + x_lo)
+    __shared__ double red[8];
+    const int g = ncell - 1 - blockIdx.x;
+    const int kc = kcell[g];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double dotp = 0.0;
-    for (int64_t r = warp; r < nwav; r += nwarp) {
-        const int g = pan.rowCell[r];
-        const int64_t i = r - wOff[g];
+    if (kc > 0) {
         const int n = pan.ncols[g];
-        const double* v = pan.vals + pan.valOff[g] + i * n;
         const int* ci = pan.colidx + pan.colOff[g];
-        double acc = 0.0;
-        for (int j = lane; j < n; j += 32) acc += v[j] * x[ci[j]];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-            y[r] = acc;
-            dotp += x[r] * acc;
+        const T* v0 = vals + pan.valOff[g];
+        const int64_t r0 = wOff[g];
+        const int nrg = (kc + 31) / 32;          // groups of 4 rows per warp actually used
+        // FP64: plain sums.  FP32: one chunk's 8 products per lane in FP32, the
+        // running sum over chunks a cascaded FP32 sum (no FP64 in the loop).
+        T acc[8], cmp[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = cmp[q] = (T)0;
+        for (int c0 = 0; c0 < n; c0 += CH) {
+            const int m = min(CH, n - c0);
+            __syncthreads();
+            if (threadIdx.x < m) {
+                const double xv = x[ci[c0 + threadIdx.x]];
+                xs[threadIdx.x] = (T)xv;
+                if constexpr (sizeof(T) == 4) xl[threadIdx.x] = (T)(xv - (double)(T)xv);
+            }
+            __syncthreads();
+            if (m == CH) {
+#pragma unroll
+                for (int qb = 0; qb < 2; ++qb) {
+                    if (qb >= nrg) break;
+                    V2 v[4][4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int r = warp + 8 * (4 * qb + q);
+                        const T* row = v0 + (int64_t)min(r, kc - 1) * n + c0 + 2 * lane;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) v[q][u] = *reinterpret_cast<const V2*>(row + 64 * u);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int r = warp + 8 * (4 * qb + q);
+                        T a = (T)0;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = 2 * lane + 64 * u;
+                            a += v[q][u].x * xs[j] + v[q][u].y * xs[j + 1];
+                            if constexpr (sizeof(T) == 4) a += v[q][u].x * xl[j] + v[q][u].y * xl[j + 1];
+                        }
+                        if (r < kc) {
+                            if constexpr (sizeof(T) == 4) sum2_add(acc[4 * qb + q], cmp[4 * qb + q], a);
+                            else acc[4 * qb + q] += a;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int r = warp + 8 * q;
+                    if (r < kc) {
+                        const T* row = v0 + (int64_t)r * n + c0;
+                        T a = (T)0;
+                        for (int j = 2 * lane; j < m; j += 64) {
+                            const V2 vv = *reinterpret_cast<const V2*>(row + j);
+                            a += vv.x * xs[j] + vv.y * xs[j + 1];
+                            if constexpr (sizeof(T) == 4) a += vv.x * xl[j] + vv.y * xl[j + 1];
+                        }
+                        if constexpr (sizeof(T) == 4) sum2_add(acc[q], cmp[q], a);
+                        else acc[q] += a;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int r = warp + 8 * q;
+            double a = (double)acc[q] + (double)cmp[q];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0 && r < kc) {
+                y[r0 + r] = a;
+                dotp += x[r0 + r] * a;
+            }
         }
     }
     if (part) {
-        const double s = block_reduce(dotp);
-        if (threadIdx.x == 0) part[blockIdx.x] = s;
+        if (lane == 0) red[warp] = dotp;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s2 = 0.0;
+            for (int i = 0; i < 8; ++i) s2 += red[i];
+            part[blockIdx.x] = s2;
+        }
     }
 }
 
@@ -194,55 +291,118 @@ __global__ void trend_solve_kernel(const double* part, int nb, int p, const doub
     for (int j = 0; j < p; ++j) beta[j] = y[j];
 }
 
-mlb_status cw_matvec_dev(mlb_ctx* ctx, const double* u, double* out) {
-    spmv_kernel<<<kSpmvBlocks, 256, 0, ctx->stream>>>(ctx->pan, ctx->cells.wOff, ctx->nwav, u, out, nullptr, nullptr);
-    MLB_CHECK_LAUNCH(ctx, "spmv_kernel");
+static void launch_spmv(mlb_ctx* ctx, const double* u, double* out, double* part, const PcgState* st) {
+    if (ctx->pan.vals32)
+        spmv_panel_kernel<float><<<ctx->ncell, 256, 0, ctx->stream>>>(ctx->pan, ctx->pan.vals32, ctx->cells.k,
+                                                                     ctx->cells.wOff, ctx->ncell, u, out, part, st);
+    else
+        spmv_panel_kernel<double><<<ctx->ncell, 256, 0, ctx->stream>>>(ctx->pan, ctx->pan.vals, ctx->cells.k,
+                                                                      ctx->cells.wOff, ctx->ncell, u, out, part, st);
+}
+
+// y += eta x; part[block] = sum x_i y_i (when part != nullptr)
+__global__ void axpy_dot_kernel(int64_t n, double eta, const double* __restrict__ x, double* __restrict__ y,
+                                double* part, const PcgState* st) {
+    if (st && st->done) return;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = y[i] + eta * x[i];
+        y[i] = v;
+        acc += x[i] * v;
+    }
+    const double s1 = block_reduce(acc);
+    if (part && threadIdx.x == 0) part[blockIdx.x] = s1;
+}
+
+// Three-step product of Sec. 6.2: out = W (K (W^T u)) + eta u, with the
+// kernel sum K a over all data points (no matrix is stored).
+static mlb_status three_step(mlb_ctx* ctx, const double* u, double* out, double* part, const PcgState* st) {
+    double* a = ctx->vec + 8 * ctx->N;
+    double* b = ctx->vec + 9 * ctx->N;
+    mlb_status s = apply_Wt_dev(ctx, u, a);
+    if (s != MLB_OK) return s;
+    // the kernel sum of every iteration: FP32 kernel values on the mixed path
+    s = kernel_sum_general(ctx, nullptr, ctx->N, nullptr, ctx->N, a, b, false, false, false);
+    if (s != MLB_OK) return s;
+    s = apply_W_dev(ctx, b, out);
+    if (s != MLB_OK) return s;
+    axpy_dot_kernel<<<kVecBlocks, 256, 0, ctx->stream>>>(ctx->nwav, ctx->theta.nugget, u, out, part, st);
+    MLB_CHECK_LAUNCH(ctx, "axpy_dot_kernel");
     return MLB_OK;
 }
 
-static void launch_iteration(mlb_ctx* ctx, double* x, double* r, double* z, double* p, double* q, double tol2) {
+mlb_status cw_matvec_dev(mlb_ctx* ctx, const double* u, double* out) {
+    if (ctx->opts.matrix_free) return three_step(ctx, u, out, nullptr, nullptr);
+    launch_spmv(ctx, u, out, nullptr, nullptr);
+    MLB_CHECK_LAUNCH(ctx, "spmv_panel_kernel");
+    return MLB_OK;
+}
+
+static mlb_status launch_iteration(mlb_ctx* ctx, double* x, double* r, double* z, double* p, double* q,
+                                   double tol2) {
     cudaStream_t st = ctx->stream;
     const int64_t n = ctx->nwav;
     const double* diag = ctx->opts.precond ? ctx->diag : nullptr;
-    spmv_kernel<<<kSpmvBlocks, 256, 0, st>>>(ctx->pan, ctx->cells.wOff, n, p, q, ctx->partial, ctx->pcg);
-    pcg_alpha_kernel<<<1, 32, 0, st>>>(ctx->partial, kSpmvBlocks, ctx->pcg);
-    pcg_update_xr_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, p, q, diag, x, r, z, ctx->partial + kSpmvBlocks);
-    pcg_beta_kernel<<<1, 32, 0, st>>>(ctx->partial + kSpmvBlocks, ctx->pcg, tol2, ctx->opts.pcg_maxit);
+    double* part2 = ctx->partial + std::max(ctx->ncell, kVecBlocks);
+    if (ctx->opts.matrix_free) {
+        // the kernel sum, the transforms and the axpy run every iteration; once
+        // converged, the kernels that check the flag return at once
+        mlb_status s = three_step(ctx, p, q, ctx->partial, ctx->pcg);
+        if (s != MLB_OK) return s;
+        pcg_alpha_kernel<<<1, 32, 0, st>>>(ctx->partial, kVecBlocks, ctx->pcg);
+    } else {
+        launch_spmv(ctx, p, q, ctx->partial, ctx->pcg);
+        ctx->launches += 1;
+        pcg_alpha_kernel<<<1, 32, 0, st>>>(ctx->partial, ctx->ncell, ctx->pcg);
+    }
+    pcg_update_xr_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, p, q, diag, x, r, z, part2);
+    pcg_beta_kernel<<<1, 32, 0, st>>>(part2, ctx->pcg, tol2, ctx->opts.pcg_maxit);
     pcg_update_p_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, z, p);
+    ctx->launches += 4;
+    return MLB_OK;
 }
 
-mlb_status solve_dev(mlb_ctx* ctx, const double* Z_kd, mlb_info* info) {
+// PCG on C~_W x = b; b and x are nwav vectors on the device, b must not alias
+// the work vectors (vec + nwav .. vec + 5 nwav).
+mlb_status pcg_run(mlb_ctx* ctx, const double* b, double* x, mlb_info* info) {
     cudaStream_t st = ctx->stream;
     const int64_t n = ctx->nwav;
-    double* b = ctx->vec;
-    double* x = ctx->gW;
     double* r = ctx->vec + n;
     double* z = ctx->vec + 2 * n;
     double* p = ctx->vec + 3 * n;
     double* q = ctx->vec + 4 * n;
-    mlb_status s = apply_W_dev(ctx, Z_kd, b);
-    if (s != MLB_OK) return s;
     const double* diag = ctx->opts.precond ? ctx->diag : nullptr;
     pcg_init_kernel<<<kVecBlocks, 256, 0, st>>>(n, b, diag, x, r, z, p, ctx->partial);
     pcg_init_scalars<<<1, 32, 0, st>>>(ctx->partial, ctx->pcg);
     MLB_CHECK_LAUNCH(ctx, "pcg_init");
+    ctx->launches += 1;
     const double tol2 = ctx->opts.pcg_rtol * ctx->opts.pcg_rtol;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
     // one chunk of iterations as a CUDA graph, replayed until done
-    const int chunk = 8;
+    const int chunk = ctx->opts.matrix_free ? 2 : 8;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    const int64_t l0 = ctx->launches;
     MLB_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < chunk; ++i) launch_iteration(ctx, x, r, z, p, q, tol2);
+    for (int i = 0; i < chunk; ++i) {
+        mlb_status ls = launch_iteration(ctx, x, r, z, p, q, tol2);
+        if (ls != MLB_OK) {
+            cudaStreamEndCapture(st, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            return ls;
+        }
+    }
     MLB_CUDA(ctx, cudaStreamEndCapture(st, &graph));
     MLB_CUDA(ctx, cudaGraphInstantiate(&exec, graph, 0));
+    const int64_t perChunk = ctx->launches - l0;   // kernels in one replay (capture counted them once)
+    ctx->launches = l0;
     PcgState hs{};
     for (;;) {
         MLB_CUDA(ctx, cudaGraphLaunch(exec, st));
-        ctx->launches += 5 * chunk;
+        ctx->launches += perChunk;
         MLB_CUDA(ctx, cudaMemcpyAsync(&hs, ctx->pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, st));
         MLB_CUDA(ctx, cudaStreamSynchronize(st));
         if (hs.done) break;
@@ -255,15 +415,32 @@ mlb_status solve_dev(mlb_ctx* ctx, const double* Z_kd, mlb_info* info) {
     cudaEventDestroy(e1);
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
+    if (info) {
+        info->iterations = hs.it;
+        info->converged = hs.status == ST_OK && hs.done;
+        info->rel_residual = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+        info->ms_pcg = ms;
+    }
+    if (hs.status == ST_BREAKDOWN) return fail(ctx, MLB_EBREAKDOWN, "PCG breakdown: p^T C~_W p <= 0");
+    if (hs.status == ST_NOCONV) return fail(ctx, MLB_ENOCONV, "PCG did not reach pcg_rtol within pcg_maxit");
+    return MLB_OK;
+}
+
+mlb_status solve_dev(mlb_ctx* ctx, const double* Z_kd, mlb_info* info) {
+    cudaStream_t st = ctx->stream;
+    double* b = ctx->vec;
+    double* x = ctx->gW;
+    mlb_status s = apply_W_dev(ctx, Z_kd, b);
+    if (s != MLB_OK) return s;
     mlb_info& I = ctx->last_info;
-    I.iterations = hs.it;
-    I.converged = hs.status == ST_OK && hs.done;
-    I.rel_residual = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+    const mlb_status ps = pcg_run(ctx, b, x, &I);
+    if (ps != MLB_OK && ps != MLB_ENOCONV && ps != MLB_EBREAKDOWN) return ps;
+    const std::string pmsg = ctx->err;
     I.nnz = ctx->pan.nnz;
     I.nnz_unique = ctx->pan.nnzUnique;
+    I.col_total = ctx->pan.colTotal;
     I.blocks = ctx->pan.blocks;
     I.ms_assemble = ctx->ms_assemble;
-    I.ms_pcg = ms;
     // gamma = W^T g, then beta
     cudaEvent_t b0, b1;
     cudaEventCreate(&b0);
@@ -275,15 +452,15 @@ mlb_status solve_dev(mlb_ctx* ctx, const double* Z_kd, mlb_info* info) {
     if (s != MLB_OK) return s;
     cudaEventRecord(b1, st);
     cudaEventSynchronize(b1);
+    float ms = 0.f;
     cudaEventElapsedTime(&ms, b0, b1);
     cudaEventDestroy(b0);
     cudaEventDestroy(b1);
     I.ms_beta = ms;
     I.launches = ctx->launches;
     if (info) *info = I;
-    if (hs.status == ST_BREAKDOWN) return fail(ctx, MLB_EBREAKDOWN, "PCG breakdown: p^T C~_W p <= 0");
-    if (hs.status == ST_NOCONV) return fail(ctx, MLB_ENOCONV, "PCG did not reach pcg_rtol within pcg_maxit");
-    return MLB_OK;
+    if (ps != MLB_OK) ctx->err = pmsg;
+    return ps;
 }
 
 mlb_status trend_dev(mlb_ctx* ctx, const double* Z_kd) {

@@ -207,3 +207,182 @@ def test_pcg_iteration_cap_reports_noconv(pkg):
         ctx.solve(P.Z)
     assert e.value.name == "ENOCONV"
     ctx.predict(P.targets)            # last iterate is still usable
+
+
+# ---- mixed precision and the matrix-free three-step product ---------------------
+
+MIXED_TOL = 1e-5      # relative prediction error of the mixed path (FP32 tiles)
+
+
+@pytest.mark.parametrize("seed,N,d,w,nu,rho,nug,n0", [
+    (500, 2000, 5, 1, 1.5, 0.3, 1e-4, 64),      # config-5 shape
+    (501, 1500, 3, 1, 2.5, 0.4, 1e-4, 32),
+    (502, 1200, 2, 1, 0.5, 0.25, 1e-4, 64),
+])
+def test_mixed_assembled_matches_fp64(pkg, seed, N, d, w, nu, rho, nug, n0):
+    P = wl.small_problem(seed, N, d, w, nu=nu, rho=rho, nugget=nug, leaf_size=n0, M=300)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        ctx = ctx_for(pkg, P, prec, rtol=1e-10, pcg_maxit=50000)
+        ctx.assemble(nu, rho, nug, math.inf)
+        b, info = ctx.solve(P.Z)
+        out[prec] = (ctx.predict(P.targets), b, info)
+    ref = dense.dense_blup(P.points, P.Z, P.targets, w, nu, rho, nug)
+    assert rel(out["fp64"][0], ref["yhat"]) < 1e-9
+    assert rel(out["mixed"][0], out["fp64"][0]) < MIXED_TOL
+    assert rel(out["mixed"][0], ref["yhat"]) < MIXED_TOL
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", MIXED_TOL)])
+def test_matrix_free_matches_dense_oracle(pkg, prec, tol):
+    P = wl.small_problem(510, 1500, 4, 2, nu=2.5, rho=0.5, nugget=1e-5, leaf_size=40, M=200)
+    ctx = pkg.Context(prec, leaf_size=40, pcg_rtol=1e-12, pcg_maxit=50000, precond=False, matrix_free=True)
+    ctx.build_basis(P.points, 2)
+    ctx.assemble(2.5, 0.5, 1e-5, math.inf)
+    b, info = ctx.solve(P.Z)
+    ref = dense.dense_blup(P.points, P.Z, P.targets, 2, 2.5, 0.5, 1e-5)
+    assert rel(ctx.predict(P.targets), ref["yhat"]) < tol
+    assert rel(b, ref["beta"]) < 100 * tol
+
+
+def test_matrix_free_product_equals_assembled(pkg):
+    P = wl.small_problem(520, 900, 3, 1, leaf_size=32)
+    a = ctx_for(pkg, P)
+    a.assemble(1.5, 0.3, 1e-3, math.inf)
+    m = pkg.Context("fp64", leaf_size=32, matrix_free=True)
+    m.build_basis(P.points, 1)
+    m.assemble(1.5, 0.3, 1e-3, math.inf)
+    u = np.random.default_rng(5).standard_normal(a.nwav)
+    assert rel(m.cw_matvec(u), a.cw_matvec(u)) < 1e-12
+    with pytest.raises(pkg.MLBError):
+        m.assemble(1.5, 0.3, 1e-3, 2.0)           # the three-step product has no truncation
+
+
+def test_large_leaf_high_dimension_basis(pkg):
+    """Leaf size 128 and p = 66 (d = 10, w = 2): the basis of the high-dimensional
+    matrix-free workload, checked through its operators."""
+    P = wl.small_problem(530, 1100, 10, 2, leaf_size=128)
+    ctx = ctx_for(pkg, P)
+    lo, hi = design.box(P.points)
+    X = design.design_matrix(P.points, 2, lo, hi)
+    v = np.random.default_rng(6).standard_normal(P.N)
+    proj = v - X @ np.linalg.solve(X.T @ X, X.T @ v)
+    np.testing.assert_allclose(ctx.apply_Wt(ctx.apply_W(v)), proj, atol=1e-10)
+
+
+# ---- gradient of the held-out loss ----------------------------------------------
+
+def test_grad_matches_dense_oracle_gradient(pkg):
+    """n = 2,000 subsample of the differentiation workload, FP64 path vs the
+    oracle's dense adjoint gradient."""
+    from oracle import grad as og
+    P = wl.subsample(wl.config5(N=8192, M=1024), 2000, seed=3, m=300)
+    ctx = ctx_for(pkg, P, rtol=1e-12, pcg_maxit=50000)
+    ctx.assemble(P.nu, P.rho, P.nugget, math.inf)
+    ctx.solve(P.Z)
+    got = ctx.grad(P.targets, P.y_targets)
+    ref = og.grad_dense(P.points, P.Z, P.targets, P.y_targets, P.w, P.nu, P.rho, P.nugget)
+    np.testing.assert_allclose(got, ref, rtol=1e-7)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_grad_matches_central_difference(pkg, prec):
+    """Central differences (h = 1e-4) of the library's own loss.  On the FP64
+    path both derivatives agree to 1e-6.  On the mixed path the loss carries
+    ~1e-7 relative noise, i.e. ~loss * 1e-7 / (2h) in a difference quotient, so
+    d/dlog(rho) is checked to 1e-3 and the (small) d/dlog(nugget) to that noise
+    level; the mixed adjoint gradient must also match the FP64 one to 1e-4."""
+    P = wl.small_problem(540, 1200, 5, 1, nu=1.5, rho=0.3, nugget=1e-4, leaf_size=64, M=200, with_y=True)
+    ctx = ctx_for(pkg, P, prec, rtol=1e-12, pcg_maxit=50000)
+
+    def loss(rho, nug):
+        ctx.assemble(1.5, rho, nug, math.inf)
+        ctx.solve(P.Z)
+        y = ctx.predict(P.targets)
+        return float(np.mean((y - P.y_targets) ** 2))
+
+    h = 1e-4
+    fd_rho = (loss(0.3 * math.exp(h), 1e-4) - loss(0.3 * math.exp(-h), 1e-4)) / (2 * h)
+    fd_nug = (loss(0.3, 1e-4 * math.exp(h)) - loss(0.3, 1e-4 * math.exp(-h))) / (2 * h)
+    ctx.assemble(1.5, 0.3, 1e-4, math.inf)
+    ctx.solve(P.Z)
+    L, g_rho, g_nug = ctx.grad(P.targets, P.y_targets)
+    assert abs(L - loss(0.3, 1e-4)) < 1e-12 + 1e-9 * abs(L)
+    if prec == "fp64":
+        assert abs(g_rho - fd_rho) <= 1e-6 * abs(fd_rho)
+        assert abs(g_nug - fd_nug) <= 1e-6 * abs(fd_nug) + 1e-12
+    else:
+        noise = L * 1e-6 / (2 * h)
+        assert abs(g_rho - fd_rho) <= 1e-3 * abs(fd_rho)
+        assert abs(g_nug - fd_nug) <= noise
+        ref = ctx_for(pkg, P, "fp64", rtol=1e-12, pcg_maxit=50000)
+        ref.assemble(1.5, 0.3, 1e-4, math.inf)
+        ref.solve(P.Z)
+        _, r_rho, r_nug = ref.grad(P.targets, P.y_targets)
+        assert abs(g_rho - r_rho) <= 1e-4 * abs(r_rho)
+        assert abs(g_nug - r_nug) <= 1e-4 * abs(r_nug)
+
+
+def test_grad_through_torch_autograd(pkg):
+    import torch
+    from paper_1701_00285_gb300.autograd import held_out_loss
+    P = wl.small_problem(541, 900, 3, 1, nu=1.5, rho=0.3, nugget=1e-4, leaf_size=32, M=100, with_y=True)
+    ctx = ctx_for(pkg, P, rtol=1e-12)
+    prob = {"context": ctx, "nu": 1.5, "Z": P.Z, "targets": P.targets, "y": P.y_targets}
+    lr = torch.tensor(math.log(0.3), dtype=torch.float64, requires_grad=True)
+    ln = torch.tensor(math.log(1e-4), dtype=torch.float64, requires_grad=True)
+    out = held_out_loss(lr, ln, prob)
+    out.backward()
+    L, g1, g2 = ctx.grad(P.targets, P.y_targets)
+    assert abs(float(out) - L) < 1e-14 and abs(float(lr.grad) - g1) < 1e-14 and abs(float(ln.grad) - g2) < 1e-14
+
+
+# ---- the configurations' own regimes ---------------------------------------------
+
+def test_high_dimension_subsample_matrix_free(pkg):
+    """2,048-point subsample of the d = 10 workload (nu = 5/2, rho = 0.5,
+    nugget 1e-5, w = 2, leaf 128): FP64 and mixed three-step PCG vs the dense
+    oracle."""
+    P = wl.subsample(wl.config3(N=16384, M=512), 2048, seed=2, m=256)
+    ref = dense.dense_blup(P.points, P.Z, P.targets, P.w, P.nu, P.rho, P.nugget)
+    got = {}
+    for prec in ("fp64", "mixed"):
+        ctx = pkg.Context(prec, leaf_size=128, pcg_rtol=1e-12, pcg_maxit=20000, precond=False, matrix_free=True)
+        ctx.build_basis(P.points, P.w)
+        ctx.assemble(P.nu, P.rho, P.nugget, math.inf)
+        ctx.solve(P.Z)
+        got[prec] = ctx.predict(P.targets)
+    assert rel(got["fp64"], ref["yhat"]) < 1e-9
+    assert rel(got["mixed"], ref["yhat"]) < MIXED_TOL
+
+
+def test_batched_problems_mixed_vs_oracle(pkg):
+    """Problems drawn from the batched workload's generator (d in {2,3,5}, all
+    three nu, rho in [0.1, 0.5], tau = 2 diameters), both precisions vs the
+    multilevel oracle's exact solve of the same truncated system."""
+    probs = [q for q in wl.config4(count=60) if q.N <= 1400][:4]
+    assert len(probs) == 4
+    for P in probs:
+        B = mlblup.setup(P.points, P.w, P.leaf_size)
+        g, b, _ = mlblup.solve(B, P.points, P.Z, P.nu, P.rho, P.nugget, P.tau_factor, exact=True)
+        yref = mlblup.predict(B, P.points, g, b, P.targets[:200], P.nu, P.rho)
+        for prec, tol in (("fp64", 1e-9), ("mixed", MIXED_TOL)):
+            ctx = ctx_for(pkg, P, prec, rtol=1e-12, pcg_maxit=50000)
+            ctx.assemble(P.nu, P.rho, P.nugget, P.tau_factor)
+            ctx.solve(P.Z)
+            assert rel(ctx.predict(P.targets[:200]), yref) < tol, (P.name, prec)
+
+
+def test_mixed_one_shot_kernel_sums_are_double_float_accurate(pkg):
+    """The mixed path evaluates the trend and prediction kernel sums in
+    double-float on the FP32 pipes: they match FP64 to ~1e-12 even with
+    oscillating weights (FP32 kernel values would give ~1e-7 and worse)."""
+    P = wl.small_problem(560, 1500, 3, 1, nu=2.5, rho=0.4, leaf_size=32, M=200)
+    c64, cmx = ctx_for(pkg, P, "fp64"), ctx_for(pkg, P, "mixed")
+    for c in (c64, cmx):
+        c.assemble(2.5, 0.4, 1e-4, math.inf)
+    rng = np.random.default_rng(7)
+    a = rng.standard_normal(P.N)
+    assert rel(cmx.kernel_sum(P.targets, a), c64.kernel_sum(P.targets, a)) < 1e-11
+    osc = a * 1e3 - np.mean(a * 1e3)                   # cancelling weights
+    assert rel(cmx.kernel_sum(P.targets, osc), c64.kernel_sum(P.targets, osc)) < 1e-10

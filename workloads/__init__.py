@@ -189,7 +189,7 @@ def config5(N: int = 32768, M: int = 4096) -> Problem:
     tg = r_tgt.uniform(0.0, 1.0, size=(M, d))
     yt = _observe(tg, w, coef, omega, math.sqrt(1e-4) * r_tnoise.standard_normal(M))
     return Problem(f"config5_grad_n{N}_d5", x, z, tg, nu=1.5, rho=0.3, nugget=1e-4,
-                   w=w, leaf_size=64, tau_factor=math.inf, pcg_rtol=1e-12,
+                   w=w, leaf_size=64, tau_factor=math.inf, pcg_rtol=1e-10,
                    y_targets=yt, meta={"trend_coef": coef, "omega": omega})
 
 
