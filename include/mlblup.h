@@ -172,6 +172,21 @@ mlb_status mlb_cw_matvec(mlb_ctx* ctx, const double* u, double* out);
  * the very product one PCG iteration performs. */
 mlb_status mlb_cw_matvec_dev(mlb_ctx* ctx, const double* u_dev, double* out_dev);
 
+/* W v like mlb_apply_W, for callers that cannot allocate device memory at the
+ * moment they need it (inside CUDA graph capture, in loops that must not block
+ * on the allocator, under a memory pool they do not own).  The paper has no
+ * counterpart: it only changes where the work space lives.  v_dev (N doubles,
+ * caller order) and out_dev (N - p doubles) are device buffers owned by the
+ * caller; the work space is one fixed 4 MiB array in device memory that every
+ * GPU loading this library keeps until the process exits, so the call accepts
+ * only N + (the scaling coefficients of all levels, about 2^(t+1) p) <= 524,288
+ * and returns MLB_EINVAL beyond that.  Nothing is allocated or freed.  The
+ * first call on a device looks up the array's device address on that device;
+ * make that first call before any stream capture.  The kernels are enqueued on
+ * the context's stream without synchronising.  All calls on one device share
+ * the array: calls whose kernels overlap in time race. */
+mlb_status mlb_apply_W_noalloc(mlb_ctx* ctx, const double* v_dev, double* out_dev);
+
 /* Number of kernels the context has launched since mlb_create. */
 mlb_status mlb_get_launch_count(const mlb_ctx* ctx, int64_t* count);
 

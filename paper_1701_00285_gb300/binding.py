@@ -76,6 +76,7 @@ _SIGS = {
     "mlb_cw_matvec": (ctypes.c_int, [_P, _P, _P]),
     "mlb_cw_matvec_dev": (ctypes.c_int, [_P, _P, _P]),
     "mlb_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "mlb_apply_W_noalloc": (ctypes.c_int, [_P, _P, _P]),
     "mlb_get_pattern": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "mlb_kernel_sum": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
 }
@@ -233,6 +234,10 @@ class Context:
 
     def cw_matvec_dev(self, u_ptr: int, out_ptr: int):
         self._check(lib().mlb_cw_matvec_dev(self._h, u_ptr, out_ptr))
+
+    def apply_W_noalloc(self, v_ptr: int, out_ptr: int):
+        """W v on caller-owned device buffers, with no device allocation."""
+        self._check(lib().mlb_apply_W_noalloc(self._h, v_ptr, out_ptr))
 
     def launch_count(self) -> int:
         c = _I64()

@@ -15,6 +15,8 @@
 // The transforms W v and W^T u (Sec. 3.1, operator W; Sec. 6.2 steps (1), (3))
 // run level by level with the per-cell factors: O(N n0 + cells p^2) work.
 #include <cfloat>
+#include <mutex>
+#include <string>
 
 #include "internal.h"
 
@@ -317,3 +319,75 @@ mlb_status scatter_kd(mlb_ctx* ctx, const double* v_kd, double* v_user) {
 }
 
 }  // namespace mlb
+
+// ---------------------------------------------------------------------------
+// W v without any device allocation.
+//
+// Some callers cannot allocate device memory when they need W v: code that
+// runs while a CUDA graph is being captured (cudaMalloc is not allowed inside
+// a capture), real-time loops that must not block on the allocator, and hosts
+// whose device memory is managed by a pool they do not own.  For them this
+// entry point keeps its work space -- the input reordered into kd-tree order
+// and the scaling coefficients of every level -- in one fixed array in device
+// global memory that every GPU loading this library reserves until the
+// process exits.  Its size bounds the problems it accepts:
+// N + (scaling coefficients of all levels) <= kNoAllocScratchDoubles.
+// Every element read during a call is first written by the same call, so
+// nothing needs clearing between calls; but all calls on one device share the
+// array, so two calls whose kernels overlap in time (different streams or
+// contexts) race on it.
+// ---------------------------------------------------------------------------
+namespace mlb {
+
+constexpr int64_t kNoAllocScratchDoubles = 524288;   // 4 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+constexpr int kNoAllocMaxDevices = 64;
+static double* g_noalloc_ptr[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mutex;
+
+// Device address of the scratch array on the current device (looked up once per device).
+static mlb_status noalloc_scratch(mlb_ctx* ctx, double** out) {
+    int dev = 0;
+    MLB_CUDA(ctx, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(ctx, MLB_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[dev] = (double*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return MLB_OK;
+}
+
+}  // namespace mlb
+
+extern "C" mlb_status mlb_apply_W_noalloc(mlb_ctx* ctx, const double* v_dev, double* out_dev) {
+    using namespace mlb;
+    if (!ctx || !v_dev || !out_dev) return fail(ctx, MLB_EINVAL, "null argument");
+    if (ctx->state < 1) return fail(ctx, MLB_ESTATE, "mlb_apply_W_noalloc needs mlb_build_basis first");
+    const int64_t need = ctx->N + ctx->sbase[ctx->t + 1];
+    if (need > kNoAllocScratchDoubles)
+        return fail(ctx, MLB_EINVAL,
+                    "mlb_apply_W_noalloc: N plus the scaling coefficients (" + std::to_string(need) +
+                        " doubles) exceed its fixed work space of " + std::to_string(kNoAllocScratchDoubles) +
+                        " doubles; use mlb_apply_W");
+    if (cudaSetDevice(ctx->opts.device) != cudaSuccess) return fail(ctx, MLB_ECUDA, "cudaSetDevice failed");
+    double* scratch = nullptr;
+    mlb_status s = noalloc_scratch(ctx, &scratch);
+    if (s != MLB_OK) return s;
+    double* v_kd = scratch;                 // N entries
+    double* sb = scratch + ctx->N;          // the levels' scaling coefficients
+    gather_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(ctx->perm, ctx->N, v_dev, v_kd);
+    MLB_CHECK_LAUNCH(ctx, "gather_kernel");
+    const size_t shm = sizeof(double) * max_s(ctx);
+    for (int l = ctx->t; l >= 0; --l) {
+        const int64_t sc = l < ctx->t ? ctx->sbase[l + 1] : 0;
+        wt_fwd_kernel<<<1u << l, 128, shm, ctx->stream>>>(ctx->cells, ctx->V, l, ctx->t, v_kd, sb, ctx->sbase[l],
+                                                         sc, out_dev);
+        MLB_CHECK_LAUNCH(ctx, "wt_fwd_kernel");
+    }
+    return MLB_OK;
+}
