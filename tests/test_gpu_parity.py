@@ -288,7 +288,8 @@ def test_grad_matches_dense_oracle_gradient(pkg):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_grad_matches_central_difference(pkg, prec):
     """Central differences (h = 1e-4) of the library's own loss.  On the FP64
-    path both derivatives agree to 1e-6.  On the mixed path the loss carries
+    path d/dlog(rho) agrees to 1e-6 and the small d/dlog(nugget) to the noise of
+    a difference quotient of a loss solved to 1e-12.  On the mixed path the loss carries
     ~1e-7 relative noise, i.e. ~loss * 1e-7 / (2h) in a difference quotient, so
     d/dlog(rho) is checked to 1e-3 and the (small) d/dlog(nugget) to that noise
     level; the mixed adjoint gradient must also match the FP64 one to 1e-4."""
@@ -309,8 +310,9 @@ def test_grad_matches_central_difference(pkg, prec):
     L, g_rho, g_nug = ctx.grad(P.targets, P.y_targets)
     assert abs(L - loss(0.3, 1e-4)) < 1e-12 + 1e-9 * abs(L)
     if prec == "fp64":
+        # PCG to 1e-12 leaves ~1e-10 relative noise in the loss: ~L 5e-7 in a quotient
         assert abs(g_rho - fd_rho) <= 1e-6 * abs(fd_rho)
-        assert abs(g_nug - fd_nug) <= 1e-6 * abs(fd_nug) + 1e-12
+        assert abs(g_nug - fd_nug) <= max(1e-6 * abs(fd_nug), L * 1e-9 / (2 * h))
     else:
         noise = L * 1e-6 / (2 * h)
         assert abs(g_rho - fd_rho) <= 1e-3 * abs(fd_rho)
