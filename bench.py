@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--single", action="store_true", help="measure only --precision")
-    ap.add_argument("--workload", default="config5", choices=["config5", "config2", "config3"])
+    ap.add_argument("--workload", default="config5", choices=["config5", "config2", "config3", "config4"])
+    ap.add_argument("--count", type=int, default=512, help="config4: number of problems")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--targets", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -297,6 +298,51 @@ def e2e_run(ctx, P, args, world, torch):
             "d2h_bytes_per_step": int(hy.nbytes + hb.nbytes)}
 
 
+def run_batched(args, rank, world, local_rank):
+    """Batched workload: every step solves all problems in one mlb_batch_solve."""
+    import torch
+    import workloads as wl
+    from paper_1701_00285_gb300.binding import batch_solve
+    torch.cuda.set_device(local_rank)
+    probs = wl.config4(count=args.count)
+    items = [{"points": q.points, "w": q.w, "nu": q.nu, "rho": q.rho, "nugget": q.nugget,
+              "tau_factor": q.tau_factor, "Z": q.Z, "targets": q.targets} for q in probs]
+    out = {}
+    for prec in ("mixed", "fp64"):
+        for _ in range(args.warmup):
+            res, ms, st = batch_solve(items, precision=prec, pcg_rtol=1e-10, pcg_maxit=50000, device=local_rank)
+        times = []
+        with ClockSampler(local_rank) as clk:
+            for _ in range(args.steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res, ms, st = batch_solve(items, precision=prec, pcg_rtol=1e-10, pcg_maxit=50000, device=local_rank)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+        out[prec] = {"res": res, "s": sum(times), "status": st, "clocks": clk.summary(),
+                     "its": [r[3] for r in res]}
+    ym = np.concatenate([r[0] for r in out["mixed"]["res"]])
+    yd = np.concatenate([r[0] for r in out["fp64"]["res"]])
+    per = [float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0])) for a, b in zip(out["mixed"]["res"], out["fp64"]["res"])]
+    value = world * args.count * args.steps / out["mixed"]["s"]
+    line = {"metric": METRIC, "value": value, "unit": "BLUP solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * out["mixed"]["s"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": f"config4: {args.count} independent problems, n log-uniform [500, 8000], "
+                                   f"d in {{2,3,5}}, nu in {{1/2,3/2,5/2}}, rho ~ U[0.1,0.5], w=1, leaf 64, "
+                                   f"tau=2 diameters, nugget 1e-4, PCG tol 1e-10, 1024 targets each",
+                       "precision": "mixed", "parallelism": f"replicas{world}",
+                       "cache": "inputs copied from the host each step (batched API takes host buffers)"},
+            "fp64": {"value": world * args.count * args.steps / out["fp64"]["s"],
+                     "ms_per_step": 1000 * out["fp64"]["s"] / args.steps},
+            "mixed_vs_fp64": {"rel_pred_err_max": max(per), "rel_pred_err_all": float(np.linalg.norm(ym - yd) / np.linalg.norm(yd)),
+                              "speedup": out["fp64"]["s"] / out["mixed"]["s"]},
+            "pcg_iterations": {"median": float(np.median(out["mixed"]["its"])), "max": int(max(out["mixed"]["its"]))},
+            "status": out["mixed"]["status"], "clocks": out["mixed"]["clocks"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1701_00285_gb300 as pkg
@@ -361,6 +407,8 @@ def main():
         dist.init_process_group(backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "config4":
+        run_batched(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

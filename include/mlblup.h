@@ -151,6 +151,35 @@ mlb_status mlb_predict_dev(mlb_ctx* ctx, const double* targets_dev, int64_t M, d
 mlb_status mlb_grad(mlb_ctx* ctx, const double* targets, int64_t M, const double* y_obs,
                     double* loss_out, double* dlogrho_out, double* dlognugget_out);
 
+/* ---- many independent problems -------------------------------------------- */
+
+typedef struct {
+    const double* points;   /* host, n x d row-major, caller order */
+    int64_t n;
+    int d;
+    int w;                  /* trend degree */
+    mlb_theta theta;
+    double tau_factor;      /* INFINITY: all pairs */
+    const double* Z;        /* host, n observations */
+    const double* targets;  /* host, m x d */
+    int64_t m;
+    double* yhat;           /* host, m predictions (output) */
+    double* beta;           /* host, p trend coefficients (output, may be NULL) */
+    int status;             /* output: this problem's mlb_status */
+    int iterations;         /* output: its PCG iterations */
+} mlb_batch_problem;
+
+/* Solves `count` independent multilevel BLUP problems (each: basis, assembly,
+ * diagonal PCG, trend step, predictions, as for a single context with
+ * `opts`).  Problems may differ in n, d, w, theta and tau.  The setup and
+ * closing phases run on `host_threads` streams in parallel; the PCG solves of
+ * all problems run in one persistent launch, one CTA per problem.  Returns
+ * MLB_OK if every problem succeeded, else the first failing status (each
+ * problem's own status is in probs[i].status).  ms_out (may be NULL): wall
+ * time of the call.  opts->matrix_free must be 0. */
+mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* probs, int count, int host_threads,
+                           double* ms_out);
+
 /* ---- inspection (tests and tools) ---------------------------------------- */
 
 /* Sizes of the current basis.  Any pointer may be NULL. */

@@ -48,6 +48,13 @@ class Info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchProblem(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int), ("w", ctypes.c_int),
+                ("theta", Theta), ("tau_factor", ctypes.c_double), ("Z", ctypes.c_void_p),
+                ("targets", ctypes.c_void_p), ("m", ctypes.c_int64), ("yhat", ctypes.c_void_p),
+                ("beta", ctypes.c_void_p), ("status", ctypes.c_int), ("iterations", ctypes.c_int)]
+
+
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
 _I64 = ctypes.c_int64
@@ -66,6 +73,8 @@ _SIGS = {
     "mlb_predict": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mlb_predict_dev": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mlb_grad": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
+    "mlb_batch_solve": (ctypes.c_int, [ctypes.POINTER(Opts), ctypes.POINTER(BatchProblem), ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "mlb_get_sizes": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(_I64)]),
@@ -108,6 +117,40 @@ def _f64(a, shape=None) -> np.ndarray:
 
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(_P)
+
+
+def batch_solve(problems, precision: str = "fp64", leaf_size: int = 64, pcg_rtol: float = 1e-10,
+                pcg_maxit: int = 20000, precond: bool = True, device: int = 0, host_threads: int = 8):
+    """Solves independent problems with mlb_batch_solve.  `problems` is a list of
+    dicts with points, w, nu, rho, nugget, tau_factor, Z, targets.  Returns
+    (list of (yhat, beta, status, iterations), wall ms)."""
+    L = lib()
+    o = Opts()
+    L.mlb_default_opts(ctypes.byref(o))
+    o.precision = MLB_MIXED if precision == "mixed" else MLB_FP64
+    o.leaf_size, o.pcg_rtol, o.pcg_maxit, o.precond, o.device = leaf_size, pcg_rtol, pcg_maxit, int(precond), device
+    keep, arr = [], (BatchProblem * len(problems))()
+    outs = []
+    for i, q in enumerate(problems):
+        pts = _f64(q["points"])
+        Z = _f64(q["Z"], (pts.shape[0],))
+        tg = _f64(q["targets"])
+        d = pts.shape[1]
+        p = math.comb(d + q["w"], q["w"])
+        y = np.empty(tg.shape[0])
+        beta = np.empty(p)
+        keep += [pts, Z, tg, y, beta]
+        a = arr[i]
+        a.points, a.n, a.d, a.w = pts.ctypes.data, pts.shape[0], d, q["w"]
+        a.theta = Theta(q["nu"], q["rho"], q["nugget"])
+        a.tau_factor = float(q.get("tau_factor", math.inf))
+        a.Z, a.targets, a.m = Z.ctypes.data, tg.ctypes.data, tg.shape[0]
+        a.yhat, a.beta = y.ctypes.data, beta.ctypes.data
+        outs.append((y, beta))
+    ms = ctypes.c_double()
+    st = L.mlb_batch_solve(ctypes.byref(o), arr, len(problems), host_threads, ctypes.byref(ms))
+    res = [(y, b, arr[i].status, arr[i].iterations) for i, (y, b) in enumerate(outs)]
+    return res, ms.value, st
 
 
 class Context:

@@ -1,0 +1,298 @@
+// Many independent BLUP problems in one call (the batched workload: problems
+// of different sizes, dimensions and covariance parameters).
+//
+// Every problem gets its own context (basis, assembly, vectors).  The setup
+// phases -- kd-tree and basis, assembly of C~_W, Z_W = W Z -- and the closing
+// phases -- gamma = W^T gamma_W, the trend step, predictions -- run the
+// single-problem kernels on a pool of streams driven by host threads.  The PCG
+// phase, where a per-problem loop would be bound by kernel launches (five
+// launches per iteration on systems of a few thousand unknowns), is one
+// persistent launch: one CTA per problem runs its whole diagonally
+// preconditioned CG (Sec. 5.2 remark, Sec. 6.2) with block-level reductions
+// only -- no CTA waits for another.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace mlb {
+
+struct BatchPcgProblem {
+    const double* vals64;      // panel values (FP64 path) or nullptr
+    const float* vals32;       // panel values (mixed path) or nullptr
+    const int* colidx;
+    const int* ncols;
+    const int64_t* valOff;
+    const int64_t* colOff;
+    const int* rowCell;
+    const int64_t* wOff;
+    const double* diag;        // nullptr: no preconditioner
+    const double* b;
+    double* x;
+    double* r;
+    double* z;
+    double* p;
+    double* q;
+    int64_t n;
+    double tol2;
+    int maxit;
+    int pad;
+    PcgState* st;
+};
+
+__device__ double cta_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) s += red[i];
+    return s;
+}
+
+// q = A p by warp-per-row over the problem's panels; returns p.q (all threads)
+__device__ double cta_spmv(const BatchPcgProblem& P, const double* __restrict__ pv, double* __restrict__ q,
+                           double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double dot = 0.0;
+    for (int64_t r = warp; r < P.n; r += nw) {
+        const int g = P.rowCell[r];
+        const int64_t i = r - P.wOff[g];
+        const int n = P.ncols[g];
+        const int* ci = P.colidx + P.colOff[g];
+        double acc = 0.0;
+        if (P.vals32) {
+            const float* v = P.vals32 + P.valOff[g] + i * n;
+            for (int j = lane; j < n; j += 32) acc += (double)v[j] * pv[ci[j]];
+        } else {
+            const double* v = P.vals64 + P.valOff[g] + i * n;
+            for (int j = lane; j < n; j += 32) acc += v[j] * pv[ci[j]];
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            q[r] = acc;
+            dot += pv[r] * acc;
+        }
+    }
+    return cta_sum(dot, red);
+}
+
+// One CTA per problem; the iteration matches pcg_run: x0 = 0, stop when
+// ||r_k||^2 <= tol^2 ||b||^2 on the recursive unpreconditioned residual.
+__global__ void __launch_bounds__(512) batch_pcg_kernel(const BatchPcgProblem* __restrict__ probs) {
+    __shared__ double red[32];
+    const BatchPcgProblem P = probs[blockIdx.x];
+    const int64_t n = P.n;
+    double rz = 0.0, bb = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double bi = P.b[i];
+        const double zi = P.diag ? bi / P.diag[i] : bi;
+        P.x[i] = 0.0;
+        P.r[i] = bi;
+        P.z[i] = zi;
+        P.p[i] = zi;
+        rz += bi * zi;
+        bb += bi * bi;
+    }
+    rz = cta_sum(rz, red);
+    bb = cta_sum(bb, red);
+    int it = 0, status = 0;
+    double rr = bb;
+    if (bb > 0.0) {
+        while (true) {
+            __syncthreads();
+            const double pq = cta_spmv(P, P.p, P.q, red);
+            if (!(pq > 0.0)) {
+                status = 1;
+                break;
+            }
+            const double alpha = rz / pq;
+            double rrl = 0.0, rzl = 0.0;
+            for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+                P.x[i] += alpha * P.p[i];
+                const double ri = P.r[i] - alpha * P.q[i];
+                P.r[i] = ri;
+                const double zi = P.diag ? ri / P.diag[i] : ri;
+                P.z[i] = zi;
+                rrl += ri * ri;
+                rzl += ri * zi;
+            }
+            rr = cta_sum(rrl, red);
+            const double rzn = cta_sum(rzl, red);
+            ++it;
+            if (rr <= P.tol2 * bb) break;
+            if (it >= P.maxit) {
+                status = 2;
+                break;
+            }
+            const double beta = rzn / rz;
+            rz = rzn;
+            for (int64_t i = threadIdx.x; i < n; i += blockDim.x) P.p[i] = P.z[i] + beta * P.p[i];
+        }
+    }
+    if (threadIdx.x == 0) {
+        P.st->it = it;
+        P.st->rr = rr;
+        P.st->bb = bb;
+        P.st->status = status;
+        P.st->done = 1;
+    }
+}
+
+}  // namespace mlb
+
+using namespace mlb;
+
+namespace {
+
+struct Job {
+    mlb_batch_problem* prob;
+    mlb_ctx* ctx = nullptr;
+    mlb_status status = MLB_OK;
+    double* Zd = nullptr;     // device Z (caller order) and kd order
+};
+
+mlb_status setup_one(Job& j, const mlb_opts& o, cudaStream_t st) {
+    mlb_batch_problem& P = *j.prob;
+    mlb_status s = mlb_create(&o, &j.ctx);
+    if (s != MLB_OK) return s;
+    mlb_set_stream(j.ctx, st);
+    s = mlb_build_basis(j.ctx, P.points, P.n, P.d, P.w);
+    if (s != MLB_OK) return s;
+    s = mlb_assemble(j.ctx, &P.theta, P.tau_factor);
+    if (s != MLB_OK) return s;
+    mlb_ctx* c = j.ctx;
+    double* Zu = c->vec + 7 * c->N;
+    double* Zkd = c->vec + 6 * c->N;
+    MLB_CUDA(c, cudaMemcpyAsync(Zu, P.Z, sizeof(double) * c->N, cudaMemcpyHostToDevice, st));
+    s = gather_kd(c, Zu, Zkd);
+    if (s != MLB_OK) return s;
+    return apply_W_dev(c, Zkd, c->vec);
+}
+
+mlb_status finish_one(Job& j) {
+    mlb_ctx* c = j.ctx;
+    mlb_batch_problem& P = *j.prob;
+    PcgState hs{};
+    MLB_CUDA(c, cudaMemcpyAsync(&hs, c->pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, c->stream));
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    P.iterations = hs.it;
+    mlb_status s = apply_Wt_dev(c, c->gW, c->gamma);
+    if (s != MLB_OK) return s;
+    s = trend_dev(c, c->vec + 6 * c->N);
+    if (s != MLB_OK) return s;
+    c->state = 3;
+    if (P.beta) {
+        MLB_CUDA(c, cudaMemcpyAsync(P.beta, c->beta, sizeof(double) * c->p, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (P.m > 0) s = mlb_predict(c, P.targets, P.m, P.yhat);
+    if (s != MLB_OK) return s;
+    if (hs.status == 1) return fail(c, MLB_EBREAKDOWN, "PCG breakdown");
+    if (hs.status == 2) return fail(c, MLB_ENOCONV, "PCG not converged");
+    return MLB_OK;
+}
+
+template <typename F>
+void run_parallel(std::vector<Job>& jobs, int threads, F f) {
+    std::atomic<int> next(0);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < threads; ++t)
+        pool.emplace_back([&, t]() {
+            for (int i = next.fetch_add(1); i < (int)jobs.size(); i = next.fetch_add(1))
+                if (jobs[i].status == MLB_OK) jobs[i].status = f(jobs[i], t);
+        });
+    for (auto& th : pool) th.join();
+}
+
+}  // namespace
+
+extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* probs, int count, int host_threads,
+                                      double* ms_out) {
+    if (!probs || count < 1) return MLB_EINVAL;
+    mlb_opts o;
+    if (opts) o = *opts;
+    else mlb_default_opts(&o);
+    if (o.matrix_free) return MLB_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (cudaSetDevice(o.device) != cudaSuccess) return MLB_ECUDA;
+    const int threads = std::max(1, std::min(host_threads > 0 ? host_threads : 8, 64));
+    std::vector<cudaStream_t> streams(threads);
+    for (auto& s : streams)
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return MLB_ECUDA;
+    std::vector<Job> jobs(count);
+    for (int i = 0; i < count; ++i) {
+        jobs[i].prob = &probs[i];
+        probs[i].status = MLB_OK;
+        probs[i].iterations = 0;
+    }
+    // phase 1: basis, assembly, Z_W
+    run_parallel(jobs, threads, [&](Job& j, int t) {
+        cudaSetDevice(o.device);
+        return setup_one(j, o, streams[t]);
+    });
+    for (auto& s : streams) cudaStreamSynchronize(s);
+    // phase 2: all PCG solves in one launch
+    std::vector<BatchPcgProblem> hp;
+    std::vector<int> idx;
+    for (int i = 0; i < count; ++i) {
+        if (jobs[i].status != MLB_OK) continue;
+        mlb_ctx* c = jobs[i].ctx;
+        BatchPcgProblem b{};
+        b.vals64 = c->pan.vals32 ? nullptr : c->pan.vals;
+        b.vals32 = c->pan.vals32;
+        b.colidx = c->pan.colidx;
+        b.ncols = c->pan.ncols;
+        b.valOff = c->pan.valOff;
+        b.colOff = c->pan.colOff;
+        b.rowCell = c->pan.rowCell;
+        b.wOff = c->cells.wOff;
+        b.diag = o.precond ? c->diag : nullptr;
+        b.n = c->nwav;
+        b.b = c->vec;
+        b.x = c->gW;
+        b.r = c->vec + b.n;
+        b.z = c->vec + 2 * b.n;
+        b.p = c->vec + 3 * b.n;
+        b.q = c->vec + 4 * b.n;
+        b.tol2 = o.pcg_rtol * o.pcg_rtol;
+        b.maxit = o.pcg_maxit;
+        b.st = c->pcg;
+        hp.push_back(b);
+        idx.push_back(i);
+    }
+    mlb_status first = MLB_OK;
+    if (!hp.empty()) {
+        BatchPcgProblem* dp = nullptr;
+        if (cudaMalloc(&dp, sizeof(BatchPcgProblem) * hp.size()) != cudaSuccess) first = MLB_ENOMEM;
+        if (first == MLB_OK) {
+            cudaMemcpy(dp, hp.data(), sizeof(BatchPcgProblem) * hp.size(), cudaMemcpyHostToDevice);
+            batch_pcg_kernel<<<(unsigned)hp.size(), 512>>>(dp);
+            const cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) first = MLB_ECUDA;
+            cudaFree(dp);
+        }
+        if (first == MLB_OK)
+            for (int i : idx) jobs[i].ctx->launches += 1;
+    }
+    // phase 3: gamma, trend, predictions
+    if (first == MLB_OK)
+        run_parallel(jobs, threads, [&](Job& j, int) {
+            cudaSetDevice(o.device);
+            return finish_one(j);
+        });
+    for (int i = 0; i < count; ++i) {
+        probs[i].status = jobs[i].status;
+        if (first == MLB_OK && jobs[i].status != MLB_OK) first = jobs[i].status;
+        if (jobs[i].ctx) mlb_destroy(jobs[i].ctx);
+    }
+    for (auto& s : streams) cudaStreamDestroy(s);
+    if (ms_out)
+        *ms_out = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return first;
+}

@@ -474,6 +474,10 @@ mlb_status mlb_assemble(mlb_ctx* ctx, const mlb_theta* th, double tau_factor) {
     ctx->state = 1;
     if (ctx->opts.matrix_free) {
         if (!std::isinf(tau_factor)) return fail(ctx, MLB_EINVAL, "the three-step product needs tau = INFINITY");
+        // the kernel sum runs in every PCG iteration: pick its launch shape now,
+        // outside the graph capture of the solve
+        mlb_status ts = tune_kernel_sum(ctx);
+        if (ts != MLB_OK) return ts;
         ctx->state = 2;
         return MLB_OK;
     }

@@ -74,6 +74,7 @@ struct mlb_ctx {
     std::string err;
     int state = 0;                 // 0 empty, 1 basis, 2 assembled, 3 solved
     int64_t launches = 0;          // kernels launched by this context
+    int ksum_variant = 1;          // launch shape of the FP32 kernel sum (autotuned)
 
     // basis
     int64_t N = 0, nwav = 0;
@@ -164,6 +165,8 @@ mlb_status kernel_sum_dev(mlb_ctx* ctx, const double* targets, int64_t M, const 
 mlb_status kernel_sum_general(mlb_ctx* ctx, const double* targets, int64_t M, const double* sources,
                               int64_t Ns, const double* weights, double* out, bool add_trend, bool deriv,
                               bool accurate = true);
+// picks the FP32 kernel-sum launch shape for this context (ksum.cu)
+mlb_status tune_kernel_sum(mlb_ctx* ctx);
 // solve.cu: PCG on C~_W x = b (nwav vectors on the device)
 mlb_status pcg_run(mlb_ctx* ctx, const double* b, double* x, mlb_info* info);
 // grad.cu

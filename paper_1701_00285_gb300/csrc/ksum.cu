@@ -1,279 +1,11 @@
-// Kernel sums out_k = sum_j phi(|y_k - x_j|) a_j over the data points (Sec.
-// 6.2: the product C gamma of the trend step, and c(x0)^T gamma of the
-// prediction, eq. Spatial), optionally plus the trend k(y_k)^T beta.
-//
-// FP64 path: one thread per target; the data points and weights stream through
-// shared memory in tiles of 128; FP64 throughout.
-// Mixed path: four targets per thread; points as FP32 offsets from the data
-// box centre (absolute error of a kernel value ~1e-7); kernel values in FP32,
-// the weights split into two FP32 numbers, the sum over one tile of 256 points
-// a cascaded FP32 sum (Sum2), the running sum over tiles in FP64.
-// Distances are formed from coordinate differences (no |x|^2 + |y|^2 - 2 x.y
-// cancellation).
-#include <cmath>
-
-#include "ff.cuh"
-#include "internal.h"
-#include "matern.cuh"
+// Kernel sums: dispatch for d <= 8, the launch-shape autotuner and the entry
+// points used by the other files (kernels in ksum_impl.cuh; d >= 9 in ksum_hi.cu).
+#include "ksum_impl.cuh"
 
 namespace mlb {
 
-struct Box3 {
-    double c[kMaxDim];
-};
-
-struct TrendArgs {
-    const double* beta;   // nullptr: no trend
-    const int* alpha;     // p x d exponents
-    int p;
-    double lo[kMaxDim], hi[kMaxDim];
-};
-
-template <int D>
-__device__ __forceinline__ void add_trend(double& acc, const double* y, const TrendArgs& tr) {
-    double u[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-        const double span = tr.hi[c] - tr.lo[c];
-        u[c] = span > 0.0 ? 2.0 * (y[c] - tr.lo[c]) / span - 1.0 : 0.0;
-    }
-    for (int m = 0; m < tr.p; ++m) {
-        double v = 1.0;
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-            for (int e = 0; e < tr.alpha[m * D + c]; ++e) v *= u[c];
-        acc += tr.beta[m] * v;
-    }
-}
-
-template <int D, bool DERIV>
-__global__ void __launch_bounds__(128) ksum_f64_kernel(const double* __restrict__ tg, int64_t M,
-                                                       const double* __restrict__ xs,
-                                                       const double* __restrict__ a, int64_t N, int kind,
-                                                       double scale, double* __restrict__ out, TrendArgs tr) {
-    __shared__ double sx[128 * D];
-    __shared__ double sa[128];
-    const int64_t k = blockIdx.x * 128LL + threadIdx.x;
-    double y[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) y[c] = k < M ? tg[k * D + c] : 0.0;
-    double acc = 0.0;
-    for (int64_t j0 = 0; j0 < N; j0 += 128) {
-        const int nj = (int)(N - j0 < 128 ? N - j0 : 128);
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < nj * D; idx += 128) sx[idx] = xs[j0 * D + idx];
-        if (threadIdx.x < nj) sa[threadIdx.x] = a[j0 + threadIdx.x];
-        __syncthreads();
-        for (int j = 0; j < nj; ++j) {
-            double r2 = 0.0;
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-                const double df = y[c] - sx[j * D + c];
-                r2 += df * df;
-            }
-            const double r = sqrt(r2);
-            acc += (DERIV ? dmatern_dlogrho_f64(r, kind, scale) : matern_f64(r, kind, scale)) * sa[j];
-        }
-    }
-    if (k >= M) return;
-    if (tr.beta) add_trend<D>(acc, y, tr);
-    out[k] = acc;
-}
-
-// Mixed: FP32 kernel values, FP32 sum per tile of 256 points, FP64 across tiles.
-template <int D, int TPT, bool DERIV>
-__global__ void __launch_bounds__(128) ksum_f32_kernel(const double* __restrict__ tg, int64_t M,
-                                                       const float* __restrict__ xs32,
-                                                       const double* __restrict__ src64,
-                                                       const double* __restrict__ a, int64_t N, int kind,
-                                                       float scale, Box3 ctr, double* __restrict__ out,
-                                                       TrendArgs tr) {
-    constexpr int TS = 256;
-    __shared__ float sx[TS * D];
-    __shared__ float sa[TS];      // weights split as a = a_hi + a_lo
-    __shared__ float sl[TS];
-    const int64_t k0 = (blockIdx.x * 128LL + threadIdx.x) * TPT;
-    float y[TPT][D];
-#pragma unroll
-    for (int t = 0; t < TPT; ++t)
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-            y[t][c] = k0 + t < M ? (float)(tg[(k0 + t) * D + c] - ctr.c[c]) : 0.0f;
-    double acc[TPT];
-#pragma unroll
-    for (int t = 0; t < TPT; ++t) acc[t] = 0.0;
-    for (int64_t j0 = 0; j0 < N; j0 += TS) {
-        const int nj = (int)(N - j0 < TS ? N - j0 : TS);
-        __syncthreads();
-        if (xs32) {
-            for (int idx = threadIdx.x; idx < nj * D; idx += 128) sx[idx] = xs32[j0 * D + idx];
-        } else {
-            for (int idx = threadIdx.x; idx < nj * D; idx += 128)
-                sx[idx] = (float)(src64[j0 * D + idx] - ctr.c[idx % D]);
-        }
-        for (int idx = threadIdx.x; idx < nj; idx += 128) {
-            const double w = a[j0 + idx];
-            const float wh = (float)w;
-            sa[idx] = wh;
-            sl[idx] = (float)(w - (double)wh);
-        }
-        __syncthreads();
-        float part[TPT], comp[TPT], low[TPT];
-#pragma unroll
-        for (int t = 0; t < TPT; ++t) part[t] = comp[t] = low[t] = 0.0f;
-        for (int j = 0; j < nj; ++j) {
-            float xj[D];
-#pragma unroll
-            for (int c = 0; c < D; ++c) xj[c] = sx[j * D + c];
-            const float aj = sa[j], alj = sl[j];
-#pragma unroll
-            for (int t = 0; t < TPT; ++t) {
-                float r2 = 0.0f;
-#pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    const float df = y[t][c] - xj[c];
-                    r2 = fmaf(df, df, r2);
-                }
-                const float r = sqrtf(r2);
-                const float kv = DERIV ? dmatern_dlogrho_f32(r, kind, scale) : matern_f32(r, kind, scale);
-                sum2_add(part[t], comp[t], __fmul_rn(kv, aj));
-                low[t] = fmaf(kv, alj, low[t]);
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < TPT; ++t) acc[t] += (double)part[t] + ((double)low[t] + (double)comp[t]);
-    }
-#pragma unroll
-    for (int t = 0; t < TPT; ++t) {
-        const int64_t k = k0 + t;
-        if (k >= M) continue;
-        double v = acc[t];
-        if (tr.beta) {
-            double yy[D];
-#pragma unroll
-            for (int c = 0; c < D; ++c) yy[c] = tg[k * D + c];
-            add_trend<D>(v, yy, tr);
-        }
-        out[k] = v;
-    }
-}
-
-// Mixed path, one-shot sums (trend step, prediction, gradient): kernel values
-// in double-float (ff.cuh) from double-float coordinates, weights split into
-// two FP32 numbers, the leading products in a cascaded sum (Sum2) over a tile
-// of 128 points with their rounding errors (TwoProduct) and the cross terms in
-// a plain FP32 sum, the running sum over tiles in FP64.  Two targets per thread.
-template <int D, int TPT, bool DERIV>
-__global__ void __launch_bounds__(128) ksum_ff_kernel(const double* __restrict__ tg, int64_t M,
-                                                      const float* __restrict__ xh32,
-                                                      const float* __restrict__ xl32,
-                                                      const double* __restrict__ src64,
-                                                      const double* __restrict__ a, int64_t N, int kind,
-                                                      double scale, Box3 ctr, double* __restrict__ out,
-                                                      TrendArgs tr) {
-    constexpr int TS = 128;
-    __shared__ float sxh[TS * D], sxl[TS * D];
-    __shared__ float sah[TS], sal[TS];
-    __shared__ float2 tab[64];
-    ff_fill_exp2_table(tab);
-    const ff sc = ff_from_double(scale);
-    const int64_t k0 = (blockIdx.x * 128LL + threadIdx.x) * TPT;
-    ff y[TPT][D];
-#pragma unroll
-    for (int t = 0; t < TPT; ++t)
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-            y[t][c] = ff_from_double(k0 + t < M ? tg[(k0 + t) * D + c] - ctr.c[c] : 0.0);
-    double acc[TPT];
-#pragma unroll
-    for (int t = 0; t < TPT; ++t) acc[t] = 0.0;
-    for (int64_t j0 = 0; j0 < N; j0 += TS) {
-        const int nj = (int)(N - j0 < TS ? N - j0 : TS);
-        __syncthreads();
-        if (xh32) {
-            for (int idx = threadIdx.x; idx < nj * D; idx += 128) {
-                sxh[idx] = xh32[j0 * D + idx];
-                sxl[idx] = xl32[j0 * D + idx];
-            }
-        } else {
-            for (int idx = threadIdx.x; idx < nj * D; idx += 128) {
-                const ff v = ff_from_double(src64[j0 * D + idx] - ctr.c[idx % D]);
-                sxh[idx] = v.h;
-                sxl[idx] = v.l;
-            }
-        }
-        for (int idx = threadIdx.x; idx < nj; idx += 128) {
-            const ff w = ff_from_double(a[j0 + idx]);
-            sah[idx] = w.h;
-            sal[idx] = w.l;
-        }
-        __syncthreads();
-        float part[TPT], comp[TPT], low[TPT];
-#pragma unroll
-        for (int t = 0; t < TPT; ++t) part[t] = comp[t] = low[t] = 0.0f;
-        for (int j = 0; j < nj; ++j) {
-            const float ah = sah[j], al = sal[j];
-#pragma unroll
-            for (int t = 0; t < TPT; ++t) {
-                ff r2 = {0.0f, 0.0f};
-#pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    ff df = ff_two_sum(y[t][c].h, -sxh[j * D + c]);
-                    df = ff_add(df, {__fsub_rn(y[t][c].l, sxl[j * D + c]), 0.0f});
-                    r2 = ff_add(r2, ff_mul(df, df));
-                }
-                const ff r = ff_sqrt(r2);
-                const ff kv = DERIV ? ff_dmatern(r, kind, sc, tab) : ff_matern(r, kind, sc, tab);
-                const float pr = __fmul_rn(kv.h, ah);
-                sum2_add(part[t], comp[t], pr);
-                low[t] = fmaf(kv.h, al, fmaf(kv.l, ah, __fadd_rn(low[t], fmaf(kv.h, ah, -pr))));
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < TPT; ++t) acc[t] += (double)part[t] + ((double)low[t] + (double)comp[t]);
-    }
-#pragma unroll
-    for (int t = 0; t < TPT; ++t) {
-        const int64_t kk = k0 + t;
-        if (kk >= M) continue;
-        double v = acc[t];
-        if (tr.beta) {
-            double yy[D];
-#pragma unroll
-            for (int c = 0; c < D; ++c) yy[c] = tg[kk * D + c];
-            add_trend<D>(v, yy, tr);
-        }
-        out[kk] = v;
-    }
-}
-
-template <int D, bool DERIV>
-static void launch_ksum(mlb_ctx* ctx, const double* tg, int64_t M, const double* src, int64_t Ns,
-                        const double* a, double* out, TrendArgs tr, bool accurate) {
-    const int kind = nu_kind(ctx->theta.nu);
-    const double scale = std::sqrt(2.0 * ctx->theta.nu) / ctx->theta.rho;
-    if (ctx->opts.precision == MLB_MIXED && accurate) {
-        Box3 ctr;
-        for (int c = 0; c < kMaxDim; ++c) ctr.c[c] = c < ctx->d ? 0.5 * (ctx->box_lo[c] + ctx->box_hi[c]) : 0.0;
-        constexpr int TPT = 2;
-        const unsigned grid = (unsigned)((M + 128 * TPT - 1) / (128 * TPT));
-        ksum_ff_kernel<D, TPT, DERIV><<<grid, 128, 0, ctx->stream>>>(
-            tg, M, src ? nullptr : ctx->xs32, src ? nullptr : ctx->xs32lo, src, a, Ns, kind, scale, ctr, out, tr);
-        return;
-    }
-    if (ctx->opts.precision == MLB_MIXED) {
-        Box3 ctr;
-        for (int c = 0; c < kMaxDim; ++c) ctr.c[c] = c < ctx->d ? 0.5 * (ctx->box_lo[c] + ctx->box_hi[c]) : 0.0;
-        constexpr int TPT = 4;
-        const unsigned grid = (unsigned)((M + 128 * TPT - 1) / (128 * TPT));
-        ksum_f32_kernel<D, TPT, DERIV><<<grid, 128, 0, ctx->stream>>>(
-            tg, M, src ? nullptr : ctx->xs32, src, a, Ns, kind, (float)scale, ctr, out, tr);
-        return;
-    }
-    const unsigned grid = (unsigned)((M + 127) / 128);
-    ksum_f64_kernel<D, DERIV><<<grid, 128, 0, ctx->stream>>>(tg, M, src ? src : ctx->xs, a, Ns, kind, scale,
-                                                              out, tr);
-}
+bool kernel_sum_hi(mlb_ctx* ctx, const double* tg, int64_t M, const double* sources, int64_t Ns,
+                   const double* weights, double* out, const TrendArgs& tr, bool deriv, bool accurate);
 
 mlb_status kernel_sum_general(mlb_ctx* ctx, const double* targets, int64_t M, const double* sources, int64_t Ns,
                               const double* weights, double* out, bool add_trend, bool deriv, bool accurate) {
@@ -296,12 +28,67 @@ mlb_status kernel_sum_general(mlb_ctx* ctx, const double* targets, int64_t M, co
         break;
         MLB_KSUM_CASE(1) MLB_KSUM_CASE(2) MLB_KSUM_CASE(3) MLB_KSUM_CASE(4)
         MLB_KSUM_CASE(5) MLB_KSUM_CASE(6) MLB_KSUM_CASE(7) MLB_KSUM_CASE(8)
-        MLB_KSUM_CASE(9) MLB_KSUM_CASE(10) MLB_KSUM_CASE(11) MLB_KSUM_CASE(12)
-        MLB_KSUM_CASE(13) MLB_KSUM_CASE(14) MLB_KSUM_CASE(15) MLB_KSUM_CASE(16)
 #undef MLB_KSUM_CASE
-        default: return fail(ctx, MLB_EINVAL, "dimension d out of range 1..16");
+        default:
+            if (ctx->d > kMaxDim || !kernel_sum_hi(ctx, tg, M, sources, Ns, weights, out, tr, deriv, accurate))
+                return fail(ctx, MLB_EINVAL, "dimension d out of range 1..16");
     }
     MLB_CHECK_LAUNCH(ctx, "kernel sum");
+    return MLB_OK;
+}
+
+// Autotuner for the FP32 kernel sum of the matrix-free product: times every
+// launch shape once on the context's own points (CUDA events on its stream)
+// and keeps the fastest, cached per (device, dimension, problem-size bucket)
+// for the rest of the process.  Runs outside any stream capture.
+static std::mutex g_tune_mutex;
+static std::map<std::tuple<int, int, int>, int> g_tune_cache;
+
+mlb_status tune_kernel_sum(mlb_ctx* ctx) {
+    ctx->ksum_variant = 1;
+    if (ctx->opts.precision != MLB_MIXED) return MLB_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int bucket = 0;
+    while ((1LL << (bucket + 1)) <= ctx->N) ++bucket;
+    const auto key = std::make_tuple(dev, ctx->d, bucket);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            ctx->ksum_variant = it->second;
+            return MLB_OK;
+        }
+    }
+    double* a = ctx->vec + 8 * ctx->N;
+    double* b = ctx->vec + 9 * ctx->N;
+    MLB_CUDA(ctx, cudaMemsetAsync(a, 0, sizeof(double) * ctx->N, ctx->stream));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bestv = 1;
+    for (int v = 0; v < kKsumVariants; ++v) {
+        ctx->ksum_variant = v;
+        mlb_status s = kernel_sum_general(ctx, nullptr, ctx->N, nullptr, ctx->N, a, b, false, false, false);
+        if (s != MLB_OK) break;
+        cudaEventRecord(e0, ctx->stream);
+        s = kernel_sum_general(ctx, nullptr, ctx->N, nullptr, ctx->N, a, b, false, false, false);
+        cudaEventRecord(e1, ctx->stream);
+        if (s != MLB_OK) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bestv = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->ksum_variant = bestv;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = bestv;
     return MLB_OK;
 }
 

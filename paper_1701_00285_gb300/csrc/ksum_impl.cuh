@@ -1,0 +1,318 @@
+// Kernel-sum kernels and launch templates, shared by ksum.cu (d <= 8) and
+// ksum_hi.cu (d >= 9), which instantiate them for disjoint dimensions so the
+// two translation units compile in parallel.
+#pragma once
+// Kernel sums out_k = sum_j phi(|y_k - x_j|) a_j over the data points (Sec.
+// 6.2: the product C gamma of the trend step, and c(x0)^T gamma of the
+// prediction, eq. Spatial), optionally plus the trend k(y_k)^T beta.
+//
+// FP64 path: one thread per target; the data points and weights stream through
+// shared memory in tiles of 128; FP64 throughout.
+// Mixed path: four targets per thread; points as FP32 offsets from the data
+// box centre (absolute error of a kernel value ~1e-7); kernel values in FP32,
+// the weights split into two FP32 numbers, the sum over one tile of 256 points
+// a cascaded FP32 sum (Sum2), the running sum over tiles in FP64.
+// Distances are formed from coordinate differences (no |x|^2 + |y|^2 - 2 x.y
+// cancellation).
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "ff.cuh"
+#include "internal.h"
+#include "matern.cuh"
+
+namespace mlb {
+
+struct Box3 {
+    double c[kMaxDim];
+};
+
+struct TrendArgs {
+    const double* beta;   // nullptr: no trend
+    const int* alpha;     // p x d exponents
+    int p;
+    double lo[kMaxDim], hi[kMaxDim];
+};
+
+template <int D>
+__device__ __forceinline__ void add_trend(double& acc, const double* y, const TrendArgs& tr) {
+    double u[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        const double span = tr.hi[c] - tr.lo[c];
+        u[c] = span > 0.0 ? 2.0 * (y[c] - tr.lo[c]) / span - 1.0 : 0.0;
+    }
+    for (int m = 0; m < tr.p; ++m) {
+        double v = 1.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            for (int e = 0; e < tr.alpha[m * D + c]; ++e) v *= u[c];
+        acc += tr.beta[m] * v;
+    }
+}
+
+template <int D, bool DERIV>
+__global__ void __launch_bounds__(128) ksum_f64_kernel(const double* __restrict__ tg, int64_t M,
+                                                       const double* __restrict__ xs,
+                                                       const double* __restrict__ a, int64_t N, int kind,
+                                                       double scale, double* __restrict__ out, TrendArgs tr) {
+    __shared__ double sx[128 * D];
+    __shared__ double sa[128];
+    const int64_t k = blockIdx.x * 128LL + threadIdx.x;
+    double y[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[c] = k < M ? tg[k * D + c] : 0.0;
+    double acc = 0.0;
+    for (int64_t j0 = 0; j0 < N; j0 += 128) {
+        const int nj = (int)(N - j0 < 128 ? N - j0 : 128);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nj * D; idx += 128) sx[idx] = xs[j0 * D + idx];
+        if (threadIdx.x < nj) sa[threadIdx.x] = a[j0 + threadIdx.x];
+        __syncthreads();
+        for (int j = 0; j < nj; ++j) {
+            double r2 = 0.0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const double df = y[c] - sx[j * D + c];
+                r2 += df * df;
+            }
+            const double r = sqrt(r2);
+            acc += (DERIV ? dmatern_dlogrho_f64(r, kind, scale) : matern_f64(r, kind, scale)) * sa[j];
+        }
+    }
+    if (k >= M) return;
+    if (tr.beta) add_trend<D>(acc, y, tr);
+    out[k] = acc;
+}
+
+// Mixed: FP32 kernel values, FP32 sum per tile of 256 points, FP64 across tiles.
+template <int D, int TPT, bool DERIV, int BS>
+__global__ void __launch_bounds__(BS) ksum_f32_kernel(const double* __restrict__ tg, int64_t M,
+                                                       const float* __restrict__ xs32,
+                                                       const double* __restrict__ src64,
+                                                       const double* __restrict__ a, int64_t N, int kind,
+                                                       float scale, Box3 ctr, double* __restrict__ out,
+                                                       TrendArgs tr) {
+    constexpr int TS = 256;
+    __shared__ float sx[TS * D];
+    __shared__ float sa[TS];      // weights split as a = a_hi + a_lo
+    __shared__ float sl[TS];
+    const int64_t k0 = (blockIdx.x * (int64_t)BS + threadIdx.x) * TPT;
+    float y[TPT][D];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t)
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            y[t][c] = k0 + t < M ? (float)(tg[(k0 + t) * D + c] - ctr.c[c]) : 0.0f;
+    double acc[TPT];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) acc[t] = 0.0;
+    for (int64_t j0 = 0; j0 < N; j0 += TS) {
+        const int nj = (int)(N - j0 < TS ? N - j0 : TS);
+        __syncthreads();
+        if (xs32) {
+            for (int idx = threadIdx.x; idx < nj * D; idx += BS) sx[idx] = xs32[j0 * D + idx];
+        } else {
+            for (int idx = threadIdx.x; idx < nj * D; idx += BS)
+                sx[idx] = (float)(src64[j0 * D + idx] - ctr.c[idx % D]);
+        }
+        for (int idx = threadIdx.x; idx < nj; idx += BS) {
+            const double w = a[j0 + idx];
+            const float wh = (float)w;
+            sa[idx] = wh;
+            sl[idx] = (float)(w - (double)wh);
+        }
+        __syncthreads();
+        float part[TPT], comp[TPT], low[TPT];
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) part[t] = comp[t] = low[t] = 0.0f;
+        for (int j = 0; j < nj; ++j) {
+            float xj[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) xj[c] = sx[j * D + c];
+            const float aj = sa[j], alj = sl[j];
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                float r2 = 0.0f;
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    const float df = y[t][c] - xj[c];
+                    r2 = fmaf(df, df, r2);
+                }
+                const float r = sqrtf(r2);
+                const float kv = DERIV ? dmatern_dlogrho_f32(r, kind, scale) : matern_f32(r, kind, scale);
+                sum2_add(part[t], comp[t], __fmul_rn(kv, aj));
+                low[t] = fmaf(kv, alj, low[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) acc[t] += (double)part[t] + ((double)low[t] + (double)comp[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int64_t k = k0 + t;
+        if (k >= M) continue;
+        double v = acc[t];
+        if (tr.beta) {
+            double yy[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) yy[c] = tg[k * D + c];
+            add_trend<D>(v, yy, tr);
+        }
+        out[k] = v;
+    }
+}
+
+// Mixed path, one-shot sums (trend step, prediction, gradient): kernel values
+// in double-float (ff.cuh) from double-float coordinates, weights split into
+// two FP32 numbers, the leading products in a cascaded sum (Sum2) over a tile
+// of 128 points with their rounding errors (TwoProduct) and the cross terms in
+// a plain FP32 sum, the running sum over tiles in FP64.  Two targets per thread.
+template <int D, int TPT, bool DERIV>
+__global__ void __launch_bounds__(128) ksum_ff_kernel(const double* __restrict__ tg, int64_t M,
+                                                      const float* __restrict__ xh32,
+                                                      const float* __restrict__ xl32,
+                                                      const double* __restrict__ src64,
+                                                      const double* __restrict__ a, int64_t N, int kind,
+                                                      double scale, Box3 ctr, double* __restrict__ out,
+                                                      TrendArgs tr) {
+    constexpr int TS = 128;
+    __shared__ float sxh[TS * D], sxl[TS * D];
+    __shared__ float sah[TS], sal[TS];
+    __shared__ float2 tab[64];
+    ff_fill_exp2_table(tab);
+    const ff sc = ff_from_double(scale);
+    const int64_t k0 = (blockIdx.x * 128LL + threadIdx.x) * TPT;
+    ff y[TPT][D];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t)
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            y[t][c] = ff_from_double(k0 + t < M ? tg[(k0 + t) * D + c] - ctr.c[c] : 0.0);
+    double acc[TPT];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) acc[t] = 0.0;
+    for (int64_t j0 = 0; j0 < N; j0 += TS) {
+        const int nj = (int)(N - j0 < TS ? N - j0 : TS);
+        __syncthreads();
+        if (xh32) {
+            for (int idx = threadIdx.x; idx < nj * D; idx += 128) {
+                sxh[idx] = xh32[j0 * D + idx];
+                sxl[idx] = xl32[j0 * D + idx];
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < nj * D; idx += 128) {
+                const ff v = ff_from_double(src64[j0 * D + idx] - ctr.c[idx % D]);
+                sxh[idx] = v.h;
+                sxl[idx] = v.l;
+            }
+        }
+        for (int idx = threadIdx.x; idx < nj; idx += 128) {
+            const ff w = ff_from_double(a[j0 + idx]);
+            sah[idx] = w.h;
+            sal[idx] = w.l;
+        }
+        __syncthreads();
+        float part[TPT], comp[TPT], low[TPT];
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) part[t] = comp[t] = low[t] = 0.0f;
+        for (int j = 0; j < nj; ++j) {
+            const float ah = sah[j], al = sal[j];
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                ff r2 = {0.0f, 0.0f};
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    ff df = ff_two_sum(y[t][c].h, -sxh[j * D + c]);
+                    df = ff_add(df, {__fsub_rn(y[t][c].l, sxl[j * D + c]), 0.0f});
+                    r2 = ff_add(r2, ff_mul(df, df));
+                }
+                const ff r = ff_sqrt(r2);
+                const ff kv = DERIV ? ff_dmatern(r, kind, sc, tab) : ff_matern(r, kind, sc, tab);
+                const float pr = __fmul_rn(kv.h, ah);
+                sum2_add(part[t], comp[t], pr);
+                low[t] = fmaf(kv.h, al, fmaf(kv.l, ah, __fadd_rn(low[t], fmaf(kv.h, ah, -pr))));
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) acc[t] += (double)part[t] + ((double)low[t] + (double)comp[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int64_t kk = k0 + t;
+        if (kk >= M) continue;
+        double v = acc[t];
+        if (tr.beta) {
+            double yy[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) yy[c] = tg[kk * D + c];
+            add_trend<D>(v, yy, tr);
+        }
+        out[kk] = v;
+    }
+}
+
+// Launch shapes of the FP32 kernel sum (targets per thread x block size); the
+// autotuner below picks one per device and dimension.  Every dimension has the
+// default (4 targets, 128 threads); the common ones have all six.
+constexpr int kKsumVariants = 6;
+constexpr int kVarTpt[kKsumVariants] = {2, 4, 8, 2, 4, 8};
+constexpr int kVarBs[kKsumVariants] = {128, 128, 128, 256, 256, 256};
+
+constexpr bool tuned_dim(int D) { return D == 2 || D == 3 || D == 4 || D == 5 || D == 6 || D == 8 || D == 10; }
+
+template <int D, bool DERIV, int TPT, int BS>
+static void launch_f32_shape(cudaStream_t st, const double* tg, int64_t M, const float* xs32, const double* src,
+                             const double* a, int64_t Ns, int kind, float scale, const Box3& ctr, double* out,
+                             const TrendArgs& tr) {
+    const unsigned grid = (unsigned)((M + (int64_t)BS * TPT - 1) / ((int64_t)BS * TPT));
+    ksum_f32_kernel<D, TPT, DERIV, BS><<<grid, BS, 0, st>>>(tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr);
+}
+
+template <int D, bool DERIV>
+static void launch_f32_variant(int v, cudaStream_t st, const double* tg, int64_t M, const float* xs32,
+                               const double* src, const double* a, int64_t Ns, int kind, float scale,
+                               const Box3& ctr, double* out, const TrendArgs& tr) {
+    if constexpr (tuned_dim(D) && !DERIV) {
+        switch (v) {
+            case 0: launch_f32_shape<D, DERIV, 2, 128>(st, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
+            case 2: launch_f32_shape<D, DERIV, 8, 128>(st, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
+            case 3: launch_f32_shape<D, DERIV, 2, 256>(st, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
+            case 4: launch_f32_shape<D, DERIV, 4, 256>(st, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
+            case 5: launch_f32_shape<D, DERIV, 8, 256>(st, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
+            default: break;
+        }
+    }
+    launch_f32_shape<D, DERIV, 4, 128>(st, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr);
+}
+
+template <int D, bool DERIV>
+static void launch_ksum(mlb_ctx* ctx, const double* tg, int64_t M, const double* src, int64_t Ns,
+                        const double* a, double* out, TrendArgs tr, bool accurate) {
+    const int kind = nu_kind(ctx->theta.nu);
+    const double scale = std::sqrt(2.0 * ctx->theta.nu) / ctx->theta.rho;
+    if (ctx->opts.precision == MLB_MIXED && accurate) {
+        Box3 ctr;
+        for (int c = 0; c < kMaxDim; ++c) ctr.c[c] = c < ctx->d ? 0.5 * (ctx->box_lo[c] + ctx->box_hi[c]) : 0.0;
+        constexpr int TPT = 2;
+        const unsigned grid = (unsigned)((M + 128 * TPT - 1) / (128 * TPT));
+        ksum_ff_kernel<D, TPT, DERIV><<<grid, 128, 0, ctx->stream>>>(
+            tg, M, src ? nullptr : ctx->xs32, src ? nullptr : ctx->xs32lo, src, a, Ns, kind, scale, ctr, out, tr);
+        return;
+    }
+    if (ctx->opts.precision == MLB_MIXED) {
+        Box3 ctr;
+        for (int c = 0; c < kMaxDim; ++c) ctr.c[c] = c < ctx->d ? 0.5 * (ctx->box_lo[c] + ctx->box_hi[c]) : 0.0;
+        launch_f32_variant<D, DERIV>(DERIV ? 1 : ctx->ksum_variant, ctx->stream, tg, M, src ? nullptr : ctx->xs32, src,
+                                     a, Ns, kind, (float)scale, ctr, out, tr);
+        return;
+    }
+    const unsigned grid = (unsigned)((M + 127) / 128);
+    ksum_f64_kernel<D, DERIV><<<grid, 128, 0, ctx->stream>>>(tg, M, src ? src : ctx->xs, a, Ns, kind, scale,
+                                                              out, tr);
+}
+
+
+}  // namespace mlb

@@ -162,6 +162,105 @@ __global__ void __launch_bounds__(256) spmv_panel_kernel(Panels pan, const T* __
     }
 }
 
+// FP32 panels: the same product with 16-byte loads of four values and all
+// eight of a warp's rows loaded before any is used (256 bytes per lane in
+// flight); x staged as FP32 high and low parts, products in FP32, each row's
+// chunk sums in a cascaded FP32 sum (Sum2), the final reduction in FP64.
+__global__ void __launch_bounds__(256) spmv_panel_f32_kernel(Panels pan, const float* __restrict__ vals,
+                                                             const int* __restrict__ kcell,
+                                                             const int64_t* __restrict__ wOff, int ncell,
+                                                             const double* __restrict__ x, double* __restrict__ y,
+                                                             double* __restrict__ part, const PcgState* st) {
+    if (st && st->done) return;
+    constexpr int CH = 256;
+    __shared__ __align__(16) float xh[CH];
+    __shared__ __align__(16) float xl[CH];
+    __shared__ double red[8];
+    const int g = ncell - 1 - blockIdx.x;
+    const int kc = kcell[g];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double dotp = 0.0;
+    if (kc > 0) {
+        const int n = pan.ncols[g];
+        const int* ci = pan.colidx + pan.colOff[g];
+        const float* v0 = vals + pan.valOff[g];
+        const int64_t r0 = wOff[g];
+        const int nq = min(8, (kc - warp + 7) / 8);    // rows of this warp: warp, warp + 8, ...
+        float acc[8], err[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = err[q] = 0.0f;
+        for (int c0 = 0; c0 < n; c0 += CH) {
+            const int m = min(CH, n - c0);
+            __syncthreads();
+            if (threadIdx.x < m) {
+                const double xv = x[ci[c0 + threadIdx.x]];
+                const float h = (float)xv;
+                xh[threadIdx.x] = h;
+                xl[threadIdx.x] = (float)(xv - (double)h);
+            }
+            __syncthreads();
+            if (m == CH) {
+                float4 v[8][2];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int r = min(warp + 8 * q, kc - 1);
+                    const float* row = v0 + (int64_t)r * n + c0 + 4 * lane;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) v[q][u] = *reinterpret_cast<const float4*>(row + 128 * u);
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (q < nq) {
+                        float a = 0.0f;
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int j = 4 * lane + 128 * u;
+                            const float4 h = *reinterpret_cast<const float4*>(xh + j);
+                            const float4 l = *reinterpret_cast<const float4*>(xl + j);
+                            a += v[q][u].x * h.x + v[q][u].y * h.y + v[q][u].z * h.z + v[q][u].w * h.w;
+                            a += v[q][u].x * l.x + v[q][u].y * l.y + v[q][u].z * l.z + v[q][u].w * l.w;
+                        }
+                        sum2_add(acc[q], err[q], a);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (q < nq) {
+                        const float* row = v0 + (int64_t)(warp + 8 * q) * n + c0;
+                        float a = 0.0f;
+                        for (int j = 4 * lane; j < m; j += 128) {
+                            const float4 vv = *reinterpret_cast<const float4*>(row + j);
+                            a += vv.x * (xh[j] + xl[j]) + vv.y * (xh[j + 1] + xl[j + 1]) +
+                                 vv.z * (xh[j + 2] + xl[j + 2]) + vv.w * (xh[j + 3] + xl[j + 3]);
+                        }
+                        sum2_add(acc[q], err[q], a);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            double a = (double)acc[q] + (double)err[q];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            const int r = warp + 8 * q;
+            if (lane == 0 && q < nq) {
+                y[r0 + r] = a;
+                dotp += x[r0 + r] * a;
+            }
+        }
+    }
+    if (part) {
+        if (lane == 0) red[warp] = dotp;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s2 = 0.0;
+            for (int i = 0; i < 8; ++i) s2 += red[i];
+            part[blockIdx.x] = s2;
+        }
+    }
+}
+
 // x = 0, r = b, z = r / diag, p = z; partials of r.z and b.b
 __global__ void pcg_init_kernel(int64_t n, const double* __restrict__ b, const double* __restrict__ diag,
                                 double* x, double* r, double* z, double* p, double* part) {
@@ -293,8 +392,8 @@ __global__ void trend_solve_kernel(const double* part, int nb, int p, const doub
 
 static void launch_spmv(mlb_ctx* ctx, const double* u, double* out, double* part, const PcgState* st) {
     if (ctx->pan.vals32)
-        spmv_panel_kernel<float><<<ctx->ncell, 256, 0, ctx->stream>>>(ctx->pan, ctx->pan.vals32, ctx->cells.k,
-                                                                     ctx->cells.wOff, ctx->ncell, u, out, part, st);
+        spmv_panel_f32_kernel<<<ctx->ncell, 256, 0, ctx->stream>>>(ctx->pan, ctx->pan.vals32, ctx->cells.k,
+                                                                  ctx->cells.wOff, ctx->ncell, u, out, part, st);
     else
         spmv_panel_kernel<double><<<ctx->ncell, 256, 0, ctx->stream>>>(ctx->pan, ctx->pan.vals, ctx->cells.k,
                                                                       ctx->cells.wOff, ctx->ncell, u, out, part, st);

@@ -388,3 +388,25 @@ def test_mixed_one_shot_kernel_sums_are_double_float_accurate(pkg):
     assert rel(cmx.kernel_sum(P.targets, a), c64.kernel_sum(P.targets, a)) < 1e-11
     osc = a * 1e3 - np.mean(a * 1e3)                   # cancelling weights
     assert rel(cmx.kernel_sum(P.targets, osc), c64.kernel_sum(P.targets, osc)) < 1e-10
+
+
+# ---- many problems in one call --------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", MIXED_TOL)])
+def test_batch_solve_matches_oracle(pkg, prec, tol):
+    """Problems of the batched workload's generator (different n, d, nu, rho;
+    tau = 2 diameters) through mlb_batch_solve, each against the multilevel
+    oracle's exact solve of its own truncated system."""
+    from paper_1701_00285_gb300.binding import batch_solve
+    probs = [q for q in wl.config4(count=80) if q.N <= 1500][:6]
+    items = [{"points": q.points, "w": q.w, "nu": q.nu, "rho": q.rho, "nugget": q.nugget,
+              "tau_factor": q.tau_factor, "Z": q.Z, "targets": q.targets[:150]} for q in probs]
+    res, ms, st = batch_solve(items, precision=prec, pcg_rtol=1e-12, pcg_maxit=50000)
+    assert st == 0 and ms > 0
+    for q, (y, b, s, its) in zip(probs, res):
+        assert s == 0 and its > 0
+        B = mlblup.setup(q.points, q.w, q.leaf_size)
+        g, bb, _ = mlblup.solve(B, q.points, q.Z, q.nu, q.rho, q.nugget, q.tau_factor, exact=True)
+        yref = mlblup.predict(B, q.points, g, bb, q.targets[:150], q.nu, q.rho)
+        assert rel(y, yref) < tol, q.name
+        assert rel(b, bb) < 1e3 * tol, q.name
