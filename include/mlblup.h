@@ -179,6 +179,8 @@ typedef struct {
  * time of the call.  opts->matrix_free must be 0. */
 mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* probs, int count, int host_threads,
                            double* ms_out);
+/* Message of the last failing mlb_batch_solve on the calling thread ("" if none). */
+const char* mlb_batch_last_error(void);
 
 /* ---- inspection (tests and tools) ---------------------------------------- */
 

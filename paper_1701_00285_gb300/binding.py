@@ -75,6 +75,7 @@ _SIGS = {
     "mlb_grad": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
     "mlb_batch_solve": (ctypes.c_int, [ctypes.POINTER(Opts), ctypes.POINTER(BatchProblem), ctypes.c_int,
                                        ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "mlb_batch_last_error": (ctypes.c_char_p, []),
     "mlb_get_sizes": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(_I64)]),
@@ -150,6 +151,9 @@ def batch_solve(problems, precision: str = "fp64", leaf_size: int = 64, pcg_rtol
     ms = ctypes.c_double()
     st = L.mlb_batch_solve(ctypes.byref(o), arr, len(problems), host_threads, ctypes.byref(ms))
     res = [(y, b, arr[i].status, arr[i].iterations) for i, (y, b) in enumerate(outs)]
+    if st != 0:
+        import warnings
+        warnings.warn("mlb_batch_solve: " + L.mlb_batch_last_error().decode())
     return res, ms.value, st
 
 

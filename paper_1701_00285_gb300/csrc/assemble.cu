@@ -614,7 +614,13 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
     int smax = 0;
     for (auto& c : ctx->hcells) smax = std::max(smax, c.s);
     const size_t cshm = sizeof(double) * ((size_t)smax * smax + (size_t)smax * 128);
-    MLB_CUDA(ctx, cudaFuncSetAttribute(cross_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cshm));
+    // the opt-in limit is a process-wide property of the kernel: contexts on
+    // other host threads would race on a per-context value, so every context
+    // requests the device maximum
+    {
+        mlb_status ss = allow_max_dynamic_smem(ctx, (const void*)cross_kernel, "cross_kernel smem");
+        if (ss != MLB_OK) return ss;
+    }
     int64_t maxX = 0;
     for (int j = t; j >= 1; --j) maxX = std::max(maxX, ctx->sumA[j - 1] * ctx->sumK[j]);
     double* X0 = (double*)dalloc(ctx, A, sizeof(double) * std::max<int64_t>(1, maxX));

@@ -268,8 +268,11 @@ mlb_status build_factors(mlb_ctx* ctx) {
     int smax = 0;
     for (auto& c : ctx->hcells) smax = c.s > smax ? c.s : smax;
     const size_t shm = sizeof(double) * ((size_t)smax * ctx->p + ctx->p + 8);
-    MLB_CUDA(ctx, cudaFuncSetAttribute(qr_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)shm));
+    if ((int)shm + 1024 > max_smem_optin()) return fail(ctx, MLB_EINVAL, "leaf_size x p too large for the basis kernel");
+    {
+        mlb_status ss = allow_max_dynamic_smem(ctx, (const void*)qr_level_kernel, "qr_level_kernel smem");
+        if (ss != MLB_OK) return ss;
+    }
     for (int l = ctx->t; l >= 0; --l) {
         qr_level_kernel<<<1u << l, 128, shm, ctx->stream>>>(ctx->cells, ctx->X, ctx->p, l, ctx->t,
                                                            ctx->V, ctx->R, ctx->flag);

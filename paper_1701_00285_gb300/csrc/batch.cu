@@ -14,6 +14,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -151,6 +152,8 @@ using namespace mlb;
 
 namespace {
 
+thread_local std::string g_batch_err;
+
 struct Job {
     mlb_batch_problem* prob;
     mlb_ctx* ctx = nullptr;
@@ -212,8 +215,11 @@ void run_parallel(std::vector<Job>& jobs, int threads, F f) {
 
 }  // namespace
 
+extern "C" const char* mlb_batch_last_error(void) { return g_batch_err.c_str(); }
+
 extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* probs, int count, int host_threads,
                                       double* ms_out) {
+    g_batch_err.clear();
     if (!probs || count < 1) return MLB_EINVAL;
     mlb_opts o;
     if (opts) o = *opts;
@@ -269,12 +275,19 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
     mlb_status first = MLB_OK;
     if (!hp.empty()) {
         BatchPcgProblem* dp = nullptr;
-        if (cudaMalloc(&dp, sizeof(BatchPcgProblem) * hp.size()) != cudaSuccess) first = MLB_ENOMEM;
+        if (cudaMalloc(&dp, sizeof(BatchPcgProblem) * hp.size()) != cudaSuccess) {
+            first = MLB_ENOMEM;
+            g_batch_err = "cudaMalloc of the problem table failed";
+        }
         if (first == MLB_OK) {
             cudaMemcpy(dp, hp.data(), sizeof(BatchPcgProblem) * hp.size(), cudaMemcpyHostToDevice);
             batch_pcg_kernel<<<(unsigned)hp.size(), 512>>>(dp);
-            const cudaError_t e = cudaDeviceSynchronize();
-            if (e != cudaSuccess) first = MLB_ECUDA;
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) {
+                first = MLB_ECUDA;
+                g_batch_err = std::string("batch_pcg_kernel: ") + cudaGetErrorString(e);
+            }
             cudaFree(dp);
         }
         if (first == MLB_OK)
@@ -288,7 +301,10 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
         });
     for (int i = 0; i < count; ++i) {
         probs[i].status = jobs[i].status;
-        if (first == MLB_OK && jobs[i].status != MLB_OK) first = jobs[i].status;
+        if (first == MLB_OK && jobs[i].status != MLB_OK) {
+            first = jobs[i].status;
+            g_batch_err = "problem " + std::to_string(i) + ": " + (jobs[i].ctx ? jobs[i].ctx->err : std::string("context"));
+        }
         if (jobs[i].ctx) mlb_destroy(jobs[i].ctx);
     }
     for (auto& s : streams) cudaStreamDestroy(s);

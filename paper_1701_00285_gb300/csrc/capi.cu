@@ -25,8 +25,25 @@ mlb_status fail(mlb_ctx* ctx, mlb_status s, const std::string& msg) {
 }
 
 mlb_status cuda_fail(mlb_ctx* ctx, cudaError_t e, const char* where) {
+    cudaGetLastError();   // a non-sticky error must not be reported again by the next launch check
     return fail(ctx, e == cudaErrorMemoryAllocation ? MLB_ENOMEM : MLB_ECUDA,
                 std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int max_smem_optin() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v > 0 ? v : 48 * 1024;
+}
+
+mlb_status allow_max_dynamic_smem(mlb_ctx* ctx, const void* func, const char* name) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, func);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem_optin() - (int)fa.sharedSizeBytes);
+    return e == cudaSuccess ? MLB_OK : cuda_fail(ctx, e, name);
 }
 
 void dfree(Arena& a, void* p) {

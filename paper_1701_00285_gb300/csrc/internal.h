@@ -126,6 +126,11 @@ mlb_status fail(mlb_ctx* ctx, mlb_status s, const std::string& msg);
 mlb_status cuda_fail(mlb_ctx* ctx, cudaError_t e, const char* where);
 void* dalloc(mlb_ctx* ctx, Arena& a, size_t bytes);
 void dfree(Arena& a, void* p);
+// largest dynamic shared memory a block may opt in to on the current device
+int max_smem_optin();
+// opts a kernel in to all the dynamic shared memory its static share leaves free;
+// one constant per kernel, so contexts on different host threads cannot race
+mlb_status allow_max_dynamic_smem(mlb_ctx* ctx, const void* func, const char* name);
 
 #define MLB_CUDA(ctx, call)                                        \
     do {                                                           \

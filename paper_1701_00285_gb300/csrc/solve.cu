@@ -164,8 +164,12 @@ __global__ void __launch_bounds__(256) spmv_panel_kernel(Panels pan, const T* __
 
 // FP32 panels: the same product with 16-byte loads of four values and all
 // eight of a warp's rows loaded before any is used (256 bytes per lane in
-// flight); x staged as FP32 high and low parts, products in FP32, each row's
-// chunk sums in a cascaded FP32 sum (Sum2), the final reduction in FP64.
+// flight).  x is staged per 256-column chunk as FP32 high and low parts in a
+// double buffer: the gather of the next chunk's x (column list -> x, an L2
+// round trip) is issued before the current chunk is multiplied and stored
+// after it, so one barrier per chunk remains and the gather latency hides
+// behind the value stream.  Products in FP32, each row's chunk sums in a
+// cascaded FP32 sum (Sum2), the final reduction in FP64.
 __global__ void __launch_bounds__(256) spmv_panel_f32_kernel(Panels pan, const float* __restrict__ vals,
                                                              const int* __restrict__ kcell,
                                                              const int64_t* __restrict__ wOff, int ncell,
@@ -173,8 +177,8 @@ __global__ void __launch_bounds__(256) spmv_panel_f32_kernel(Panels pan, const f
                                                              double* __restrict__ part, const PcgState* st) {
     if (st && st->done) return;
     constexpr int CH = 256;
-    __shared__ __align__(16) float xh[CH];
-    __shared__ __align__(16) float xl[CH];
+    __shared__ __align__(16) float xh[2][CH];
+    __shared__ __align__(16) float xl[2][CH];
     __shared__ double red[8];
     const int g = ncell - 1 - blockIdx.x;
     const int kc = kcell[g];
@@ -189,16 +193,22 @@ __global__ void __launch_bounds__(256) spmv_panel_f32_kernel(Panels pan, const f
         float acc[8], err[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[q] = err[q] = 0.0f;
+        // stage chunk 0
+        if (threadIdx.x < min(CH, n)) {
+            const double xv = x[ci[threadIdx.x]];
+            const float h = (float)xv;
+            xh[0][threadIdx.x] = h;
+            xl[0][threadIdx.x] = (float)(xv - (double)h);
+        }
+        __syncthreads();
+        int buf = 0;
         for (int c0 = 0; c0 < n; c0 += CH) {
             const int m = min(CH, n - c0);
-            __syncthreads();
-            if (threadIdx.x < m) {
-                const double xv = x[ci[c0 + threadIdx.x]];
-                const float h = (float)xv;
-                xh[threadIdx.x] = h;
-                xl[threadIdx.x] = (float)(xv - (double)h);
-            }
-            __syncthreads();
+            // gather of the next chunk, consumed after this chunk's products
+            const int cn = c0 + CH + threadIdx.x;
+            const double xn = cn < n ? x[ci[cn]] : 0.0;
+            const float* sh = xh[buf];
+            const float* sl = xl[buf];
             if (m == CH) {
                 float4 v[8][2];
 #pragma unroll
@@ -215,8 +225,8 @@ __global__ void __launch_bounds__(256) spmv_panel_f32_kernel(Panels pan, const f
 #pragma unroll
                         for (int u = 0; u < 2; ++u) {
                             const int j = 4 * lane + 128 * u;
-                            const float4 h = *reinterpret_cast<const float4*>(xh + j);
-                            const float4 l = *reinterpret_cast<const float4*>(xl + j);
+                            const float4 h = *reinterpret_cast<const float4*>(sh + j);
+                            const float4 l = *reinterpret_cast<const float4*>(sl + j);
                             a += v[q][u].x * h.x + v[q][u].y * h.y + v[q][u].z * h.z + v[q][u].w * h.w;
                             a += v[q][u].x * l.x + v[q][u].y * l.y + v[q][u].z * l.z + v[q][u].w * l.w;
                         }
@@ -231,13 +241,20 @@ __global__ void __launch_bounds__(256) spmv_panel_f32_kernel(Panels pan, const f
                         float a = 0.0f;
                         for (int j = 4 * lane; j < m; j += 128) {
                             const float4 vv = *reinterpret_cast<const float4*>(row + j);
-                            a += vv.x * (xh[j] + xl[j]) + vv.y * (xh[j + 1] + xl[j + 1]) +
-                                 vv.z * (xh[j + 2] + xl[j + 2]) + vv.w * (xh[j + 3] + xl[j + 3]);
+                            a += vv.x * (sh[j] + sl[j]) + vv.y * (sh[j + 1] + sl[j + 1]) +
+                                 vv.z * (sh[j + 2] + sl[j + 2]) + vv.w * (sh[j + 3] + sl[j + 3]);
                         }
                         sum2_add(acc[q], err[q], a);
                     }
                 }
             }
+            if (cn < n) {
+                const float h = (float)xn;
+                xh[buf ^ 1][threadIdx.x] = h;
+                xl[buf ^ 1][threadIdx.x] = (float)(xn - (double)h);
+            }
+            __syncthreads();
+            buf ^= 1;
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {

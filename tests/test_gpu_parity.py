@@ -402,7 +402,8 @@ def test_batch_solve_matches_oracle(pkg, prec, tol):
     items = [{"points": q.points, "w": q.w, "nu": q.nu, "rho": q.rho, "nugget": q.nugget,
               "tau_factor": q.tau_factor, "Z": q.Z, "targets": q.targets[:150]} for q in probs]
     res, ms, st = batch_solve(items, precision=prec, pcg_rtol=1e-12, pcg_maxit=50000)
-    assert st == 0 and ms > 0
+    from paper_1701_00285_gb300 import lib
+    assert st == 0 and ms > 0, lib().mlb_batch_last_error().decode()
     for q, (y, b, s, its) in zip(probs, res):
         assert s == 0 and its > 0
         B = mlblup.setup(q.points, q.w, q.leaf_size)
