@@ -25,7 +25,9 @@
 //
 // Storage: one dense row panel per cell (k_c rows, the admissible blocks side
 // by side in global column order) plus one column-index list per panel.
+#include <algorithm>
 #include <cmath>
+#include <utility>
 
 #include "internal.h"
 #include "ff.cuh"
@@ -651,7 +653,23 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
     dfree(A, X0);
     dfree(A, X1);
     if (mixed) {
-        // the mixed path keeps C~_W in FP32: half the bytes per product
+        // the mixed path keeps C~_W in FP32: half the bytes per product.  Its
+        // product runs one CTA per 32 rows of a panel, heaviest items first.
+        std::vector<std::pair<int64_t, int2>> items;
+        for (int g = 0; g < ncell; ++g)
+            for (int r = 0; r < ctx->hcells[g].k; r += 32)
+                items.push_back({-(int64_t)std::min(32, ctx->hcells[g].k - r) * padded[g], make_int2(g, r)});
+        std::stable_sort(items.begin(), items.end(),
+                         [](const std::pair<int64_t, int2>& x, const std::pair<int64_t, int2>& y) {
+                             return x.first < y.first;
+                         });
+        std::vector<int2> work;
+        for (auto& it : items) work.push_back(it.second);
+        pan.nwork = (int)work.size();
+        pan.work = (int2*)dalloc(ctx, A, sizeof(int2) * std::max<size_t>(1, work.size()));
+        if (!pan.work) return MLB_ENOMEM;
+        MLB_CUDA(ctx, cudaMemcpyAsync(pan.work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, st));
+        MLB_CUDA(ctx, cudaStreamSynchronize(st));
         pan.vals32 = (float*)dalloc(ctx, A, sizeof(float) * std::max<int64_t>(1, stored));
         if (!pan.vals32) return MLB_ENOMEM;
         to_f32_kernel<<<1216, 256, 0, st>>>(pan.vals, std::max<int64_t>(1, stored), pan.vals32);

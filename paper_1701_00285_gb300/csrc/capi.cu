@@ -338,7 +338,7 @@ static mlb_status build_basis_host(mlb_ctx* ctx, const double* pts, int64_t N, i
     ctx->gamma = (double*)dalloc(ctx, A, sizeof(double) * N);
     ctx->beta = (double*)dalloc(ctx, A, sizeof(double) * p);
     ctx->vec = (double*)dalloc(ctx, A, sizeof(double) * 10 * N);
-    ctx->partial = (double*)dalloc(ctx, A, sizeof(double) * ((size_t)ncell + 16384));
+    ctx->partial = (double*)dalloc(ctx, A, sizeof(double) * (max_work_items(ncell, N) + 16384));
     ctx->pcg = (PcgState*)dalloc(ctx, A, sizeof(PcgState));
     CellTables& C = ctx->cells;
     C.beg = (int*)dalloc(ctx, A, sizeof(int) * ncell);

@@ -53,7 +53,13 @@ struct Panels {
     int* rowCell = nullptr;     // per wavelet row: its cell
     double* vals = nullptr;     // FP64 values
     float* vals32 = nullptr;    // FP32 copy (mixed precision)
+    int2* work = nullptr;       // FP32 product: (cell, first row) of each CTA, heaviest first
+    int nwork = 0;
 };
+
+// Upper bound on the FP32 product's work items (at most 32 rows each): the
+// cells hold nwav <= N rows, so sum over cells of ceil(k / 32) <= ncell + N / 32.
+inline size_t max_work_items(int ncell, int64_t N) { return (size_t)ncell + (size_t)(N / 32) + 1; }
 
 struct PcgState {
     double rz, rr, bb, alpha, beta, pq;

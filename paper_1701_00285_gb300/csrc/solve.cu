@@ -162,17 +162,18 @@ __global__ void __launch_bounds__(256) spmv_panel_kernel(Panels pan, const T* __
     }
 }
 
-// FP32 panels: the same product with 16-byte loads of four values and all
-// eight of a warp's rows loaded before any is used (256 bytes per lane in
-// flight).  x is staged per 256-column chunk as FP32 high and low parts in a
-// double buffer: the gather of the next chunk's x (column list -> x, an L2
-// round trip) is issued before the current chunk is multiplied and stored
-// after it, so one barrier per chunk remains and the gather latency hides
-// behind the value stream.  Products in FP32, each row's chunk sums in a
-// cascaded FP32 sum (Sum2), the final reduction in FP64.
+// FP32 panels: one CTA per work item of at most 32 rows of a panel (the
+// heaviest items first, so that the uneven panels fill the SMs evenly); each
+// warp owns four rows and loads, per 256-column chunk, two 16-byte vectors of
+// each of them before using any (128 bytes per lane in flight).  x is staged
+// per chunk as FP32 high and low parts in a double buffer: the gather of the
+// next chunk's x (column list -> x, an L2 round trip) is issued before the
+// current chunk is multiplied and stored after it, so one barrier per chunk
+// remains and the gather hides behind the value stream.  Products in FP32,
+// each row's chunk sums in a cascaded FP32 sum (Sum2), the reduction in FP64.
 __global__ void __launch_bounds__(256) spmv_panel_f32_kernel(Panels pan, const float* __restrict__ vals,
                                                              const int* __restrict__ kcell,
-                                                             const int64_t* __restrict__ wOff, int ncell,
+                                                             const int64_t* __restrict__ wOff,
                                                              const double* __restrict__ x, double* __restrict__ y,
                                                              double* __restrict__ part, const PcgState* st) {
     if (st && st->done) return;
@@ -180,91 +181,89 @@ __global__ void __launch_bounds__(256) spmv_panel_f32_kernel(Panels pan, const f
     __shared__ __align__(16) float xh[2][CH];
     __shared__ __align__(16) float xl[2][CH];
     __shared__ double red[8];
-    const int g = ncell - 1 - blockIdx.x;
-    const int kc = kcell[g];
+    const int2 wk = pan.work[blockIdx.x];
+    const int g = wk.x;
+    const int rows = min(32, kcell[g] - wk.y);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double dotp = 0.0;
-    if (kc > 0) {
-        const int n = pan.ncols[g];
-        const int* ci = pan.colidx + pan.colOff[g];
-        const float* v0 = vals + pan.valOff[g];
-        const int64_t r0 = wOff[g];
-        const int nq = min(8, (kc - warp + 7) / 8);    // rows of this warp: warp, warp + 8, ...
-        float acc[8], err[8];
+    const int n = pan.ncols[g];
+    const int* ci = pan.colidx + pan.colOff[g];
+    const int64_t nn = n;
+    const float* v0 = vals + pan.valOff[g] + (int64_t)wk.y * nn;
+    const int64_t r0 = wOff[g] + wk.y;
+    const int nq = min(4, (rows - warp + 7) / 8);      // rows of this warp: warp, warp + 8, ...
+    float acc[4], err[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = err[q] = 0.0f;
-        // stage chunk 0
-        if (threadIdx.x < min(CH, n)) {
-            const double xv = x[ci[threadIdx.x]];
-            const float h = (float)xv;
-            xh[0][threadIdx.x] = h;
-            xl[0][threadIdx.x] = (float)(xv - (double)h);
+    for (int q = 0; q < 4; ++q) acc[q] = err[q] = 0.0f;
+    if (threadIdx.x < min(CH, n)) {
+        const double xv = x[ci[threadIdx.x]];
+        const float h = (float)xv;
+        xh[0][threadIdx.x] = h;
+        xl[0][threadIdx.x] = (float)(xv - (double)h);
+    }
+    __syncthreads();
+    int buf = 0;
+    for (int c0 = 0; c0 < n; c0 += CH) {
+        const int m = min(CH, n - c0);
+        const int cn = c0 + CH + threadIdx.x;
+        const double xn = cn < n ? x[ci[cn]] : 0.0;
+        const float* sh = xh[buf];
+        const float* sl = xl[buf];
+        if (m == CH) {
+            float4 v[4][2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = min(warp + 8 * q, rows - 1);
+                const float* row = v0 + (int64_t)r * nn + c0 + 4 * lane;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) v[q][u] = *reinterpret_cast<const float4*>(row + 128 * u);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q < nq) {
+                    float a = 0.0f;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int j = 4 * lane + 128 * u;
+                        const float4 h = *reinterpret_cast<const float4*>(sh + j);
+                        const float4 l = *reinterpret_cast<const float4*>(sl + j);
+                        a += v[q][u].x * h.x + v[q][u].y * h.y + v[q][u].z * h.z + v[q][u].w * h.w;
+                        a += v[q][u].x * l.x + v[q][u].y * l.y + v[q][u].z * l.z + v[q][u].w * l.w;
+                    }
+                    sum2_add(acc[q], err[q], a);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q < nq) {
+                    const float* row = v0 + (int64_t)(warp + 8 * q) * nn + c0;
+                    float a = 0.0f;
+                    for (int j = 4 * lane; j < m; j += 128) {
+                        const float4 vv = *reinterpret_cast<const float4*>(row + j);
+                        a += vv.x * (sh[j] + sl[j]) + vv.y * (sh[j + 1] + sl[j + 1]) +
+                             vv.z * (sh[j + 2] + sl[j + 2]) + vv.w * (sh[j + 3] + sl[j + 3]);
+                    }
+                    sum2_add(acc[q], err[q], a);
+                }
+            }
+        }
+        if (cn < n) {
+            const float h = (float)xn;
+            xh[buf ^ 1][threadIdx.x] = h;
+            xl[buf ^ 1][threadIdx.x] = (float)(xn - (double)h);
         }
         __syncthreads();
-        int buf = 0;
-        for (int c0 = 0; c0 < n; c0 += CH) {
-            const int m = min(CH, n - c0);
-            // gather of the next chunk, consumed after this chunk's products
-            const int cn = c0 + CH + threadIdx.x;
-            const double xn = cn < n ? x[ci[cn]] : 0.0;
-            const float* sh = xh[buf];
-            const float* sl = xl[buf];
-            if (m == CH) {
-                float4 v[8][2];
+        buf ^= 1;
+    }
+    double dotp = 0.0;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int r = min(warp + 8 * q, kc - 1);
-                    const float* row = v0 + (int64_t)r * n + c0 + 4 * lane;
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) v[q][u] = *reinterpret_cast<const float4*>(row + 128 * u);
-                }
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if (q < nq) {
-                        float a = 0.0f;
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            const int j = 4 * lane + 128 * u;
-                            const float4 h = *reinterpret_cast<const float4*>(sh + j);
-                            const float4 l = *reinterpret_cast<const float4*>(sl + j);
-                            a += v[q][u].x * h.x + v[q][u].y * h.y + v[q][u].z * h.z + v[q][u].w * h.w;
-                            a += v[q][u].x * l.x + v[q][u].y * l.y + v[q][u].z * l.z + v[q][u].w * l.w;
-                        }
-                        sum2_add(acc[q], err[q], a);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if (q < nq) {
-                        const float* row = v0 + (int64_t)(warp + 8 * q) * n + c0;
-                        float a = 0.0f;
-                        for (int j = 4 * lane; j < m; j += 128) {
-                            const float4 vv = *reinterpret_cast<const float4*>(row + j);
-                            a += vv.x * (sh[j] + sl[j]) + vv.y * (sh[j + 1] + sl[j + 1]) +
-                                 vv.z * (sh[j + 2] + sl[j + 2]) + vv.w * (sh[j + 3] + sl[j + 3]);
-                        }
-                        sum2_add(acc[q], err[q], a);
-                    }
-                }
-            }
-            if (cn < n) {
-                const float h = (float)xn;
-                xh[buf ^ 1][threadIdx.x] = h;
-                xl[buf ^ 1][threadIdx.x] = (float)(xn - (double)h);
-            }
-            __syncthreads();
-            buf ^= 1;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            double a = (double)acc[q] + (double)err[q];
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            const int r = warp + 8 * q;
-            if (lane == 0 && q < nq) {
-                y[r0 + r] = a;
-                dotp += x[r0 + r] * a;
-            }
+    for (int q = 0; q < 4; ++q) {
+        double a = (double)acc[q] + (double)err[q];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        const int r = warp + 8 * q;
+        if (lane == 0 && q < nq) {
+            y[r0 + r] = a;
+            dotp += x[r0 + r] * a;
         }
     }
     if (part) {
@@ -408,10 +407,14 @@ __global__ void trend_solve_kernel(const double* part, int nb, int p, const doub
 }
 
 static void launch_spmv(mlb_ctx* ctx, const double* u, double* out, double* part, const PcgState* st) {
-    if (ctx->pan.vals32)
-        spmv_panel_f32_kernel<<<ctx->ncell, 256, 0, ctx->stream>>>(ctx->pan, ctx->pan.vals32, ctx->cells.k,
-                                                                  ctx->cells.wOff, ctx->ncell, u, out, part, st);
-    else
+    if (ctx->pan.vals32) {
+        if (ctx->pan.nwork == 0) {    // no wavelet rows: an empty product, a zero dot
+            if (part) cudaMemsetAsync(part, 0, sizeof(double), ctx->stream);
+            return;
+        }
+        spmv_panel_f32_kernel<<<ctx->pan.nwork, 256, 0, ctx->stream>>>(ctx->pan, ctx->pan.vals32, ctx->cells.k,
+                                                                      ctx->cells.wOff, u, out, part, st);
+    } else
         spmv_panel_kernel<double><<<ctx->ncell, 256, 0, ctx->stream>>>(ctx->pan, ctx->pan.vals, ctx->cells.k,
                                                                       ctx->cells.wOff, ctx->ncell, u, out, part, st);
 }
@@ -459,7 +462,7 @@ static mlb_status launch_iteration(mlb_ctx* ctx, double* x, double* r, double* z
     cudaStream_t st = ctx->stream;
     const int64_t n = ctx->nwav;
     const double* diag = ctx->opts.precond ? ctx->diag : nullptr;
-    double* part2 = ctx->partial + std::max(ctx->ncell, kVecBlocks);
+    double* part2 = ctx->partial + std::max(max_work_items(ctx->ncell, ctx->N), (size_t)kVecBlocks);
     if (ctx->opts.matrix_free) {
         // the kernel sum, the transforms and the axpy run every iteration; once
         // converged, the kernels that check the flag return at once
@@ -469,7 +472,8 @@ static mlb_status launch_iteration(mlb_ctx* ctx, double* x, double* r, double* z
     } else {
         launch_spmv(ctx, p, q, ctx->partial, ctx->pcg);
         ctx->launches += 1;
-        pcg_alpha_kernel<<<1, 32, 0, st>>>(ctx->partial, ctx->ncell, ctx->pcg);
+        pcg_alpha_kernel<<<1, 32, 0, st>>>(ctx->partial, ctx->pan.vals32 ? std::max(ctx->pan.nwork, 1) : ctx->ncell,
+                                           ctx->pcg);
     }
     pcg_update_xr_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, p, q, diag, x, r, z, part2);
     pcg_beta_kernel<<<1, 32, 0, st>>>(part2, ctx->pcg, tol2, ctx->opts.pcg_maxit);

@@ -1,0 +1,67 @@
+"""Micro-benchmark of the PCG operator product C~_W u (Sec. 6, Eq. 17).
+
+Builds the multilevel basis and assembles C~_W for a seeded dense-pattern
+problem (all level pairs admissible, tau = infinity), then times
+``mlb_cw_matvec_dev`` on the device with CUDA events on the context's stream.
+The panels are larger than the L2 cache at the default size, so every call
+streams them from HBM.  One JSON line per precision:
+
+    python -m paper_1701_00285_gb300.matvec_bench --n 32768 --precision mixed --reps 20
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+
+def main(argv=None) -> None:
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--n", type=int, default=32768, help="observations")
+    ap.add_argument("--precision", default="mixed,fp64", help="comma list of mixed, fp64")
+    ap.add_argument("--reps", type=int, default=20, help="timed products")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--leaf-size", type=int, default=64)
+    a = ap.parse_args(argv)
+
+    import torch
+    import workloads as wl
+    from .binding import Context
+
+    P = wl.config5(N=a.n, M=512)
+    st = torch.cuda.Stream()
+    for prec in a.precision.split(","):
+        c = Context(prec, leaf_size=a.leaf_size)
+        try:
+            c.set_stream(st.cuda_stream)
+            c.build_basis(P.points, 1)
+            c.assemble(P.nu, P.rho, P.nugget, math.inf)
+            nw = c.nwav
+            with torch.cuda.stream(st):
+                u = torch.randn(nw, dtype=torch.float64, device="cuda",
+                                generator=torch.Generator("cuda").manual_seed(1))
+                o = torch.empty_like(u)
+            st.synchronize()
+            for _ in range(a.warmup):
+                c.cw_matvec_dev(u.data_ptr(), o.data_ptr())
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(a.reps):
+                c.cw_matvec_dev(u.data_ptr(), o.data_ptr())
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / max(a.reps, 1)
+            vb = 4 if prec == "mixed" else 8
+            # tau = infinity makes the pattern dense: nwav^2 entries.  Algorithmic
+            # bytes: every entry once, u read and C~_W u written.
+            nnz = nw * nw
+            algo = nnz * vb + 2 * nw * 8
+            print(json.dumps({"precision": prec, "n": a.n, "nwav": nw, "nnz": nnz, "ms": ms,
+                              "algorithmic_bytes": algo, "GBps": algo / ms / 1e6}), flush=True)
+        finally:
+            c.close()
+
+
+if __name__ == "__main__":
+    main()
