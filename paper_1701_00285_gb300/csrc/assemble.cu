@@ -283,6 +283,95 @@ __global__ void __launch_bounds__(256) galerkin_tile_kernel(CellTables C, int le
     }
 }
 
+// Coarse levels: G = V_f^T H V_e with H the children's SS block, for cells
+// of at most SM <= 32 basis vectors (s = a_left + a_right <= 2p).  A group of
+// SM*SM/8 threads owns one pair and each thread a 2 x 4 micro-tile, so one
+// 256-thread CTA works on 256 / (SM*SM/8) pairs at once (8 at SM = 16, 2 at
+// SM = 32) instead of padding every pair to a 64 x 64 tile.  The sums run
+// over the pair's own sizes, in the same order as the padded kernel.
+template <int SM>
+__global__ void __launch_bounds__(256) galerkin_level_kernel(CellTables C, int level, int64_t npairs,
+                                                             TileIn in, TileOut out) {
+    constexpr int G = SM * SM / 8;        // threads per pair
+    constexpr int PPC = 256 / G;          // pairs per CTA
+    constexpr int CG = SM / 4;            // column groups of a micro-tile row
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int grp = threadIdx.x / G, t = threadIdx.x % G;
+    double* Vf = reinterpret_cast<double*>(smraw) + grp * 3 * SM * SM;
+    double* Ve = Vf + SM * SM;
+    double* P = Ve + SM * SM;
+    const int r0 = 2 * (t / CG), c0 = 4 * (t % CG);
+    const int first = (1 << level) - 1;
+    for (int64_t base = (int64_t)blockIdx.x * PPC; base < npairs; base += (int64_t)gridDim.x * PPC) {
+        const int64_t pi = base + grp;
+        const bool live = pi < npairs;
+        int gf = first, ge = first, sf = 0, se = 0, af = 0, ae = 0;
+        if (live) {
+            int f, e;
+            unrank_pair(pi, f, e);
+            gf = first + f;
+            ge = first + e;
+            sf = C.s[gf];
+            se = C.s[ge];
+            af = C.a[gf];
+            ae = C.a[ge];
+            const double* gVf = in.V + C.vOff[gf];
+            const double* gVe = in.V + C.vOff[ge];
+            const int64_t row0 = C.sOff[2 * gf + 1], col0 = C.sOff[2 * ge + 1];
+            for (int idx = t; idx < SM * SM; idx += G) {
+                const int r = idx / SM, c = idx % SM;
+                Vf[idx] = (r < sf && c < sf) ? gVf[r * sf + c] : 0.0;
+                Ve[idx] = (r < se && c < se) ? gVe[r * se + c] : 0.0;
+                P[idx] = (r < sf && c < se) ? in.SSc[(row0 + r) * in.ldSSc + col0 + c] : 0.0;
+            }
+        }
+        __syncthreads();
+        double acc[2][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int k = 0; k < se; ++k) {      // T = H V_e
+            const double a0 = P[r0 * SM + k], a1 = P[(r0 + 1) * SM + k];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const double b = Ve[k * SM + c0 + j];
+                acc[0][j] += a0 * b;
+                acc[1][j] += a1 * b;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                P[(r0 + i) * SM + c0 + j] = acc[i][j];
+                acc[i][j] = 0.0;
+            }
+        __syncthreads();
+        for (int k = 0; k < sf; ++k) {      // G = V_f^T T
+            const double a0 = Vf[k * SM + r0], a1 = Vf[k * SM + r0 + 1];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const double b = P[k * SM + c0 + j];
+                acc[0][j] += a0 * b;
+                acc[1][j] += a1 * b;
+            }
+        }
+        if (live) {
+            const bool diagPair = (gf == ge);
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int r = r0 + i, c = c0 + j;
+                    if (r < sf && c < se) put_entry(C, out, gf, ge, diagPair, af, ae, r, c, acc[i][j]);
+                }
+        }
+        __syncthreads();
+    }
+}
+
 // Mixed leaf pass: G = V_f^T Phi V_e on the FP32 pipes.  Phi is evaluated in
 // double-float (ff.cuh): coordinates as double-float offsets from the leaf
 // centres plus the double-float difference of the two centres, distance,
@@ -608,7 +697,19 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
         } else {
             in.SSc = SS[l + 1];
             in.ldSSc = ctx->sumA[l + 1];
-            galerkin_tile_kernel<false><<<grid, 256, shm, st>>>(ctx->cells, l, npairs, in, o);
+            int smax = 0;
+            for (int64_t k = 0; k < L; ++k) smax = std::max(smax, ctx->hcells[L - 1 + k].s);
+            // small coarse cells: several pairs per CTA at their own size
+            const size_t lshm = sizeof(double) * 3 * 256 * 8;    // 3 SM^2 doubles per pair, 256/(SM^2/8) pairs
+            if (smax <= 16) {
+                const unsigned lg = (unsigned)std::min<int64_t>((npairs + 7) / 8, (int64_t)nsm * 16);
+                galerkin_level_kernel<16><<<lg, 256, lshm, st>>>(ctx->cells, l, npairs, in, o);
+            } else if (smax <= 32) {
+                const unsigned lg = (unsigned)std::min<int64_t>((npairs + 1) / 2, (int64_t)nsm * 16);
+                galerkin_level_kernel<32><<<lg, 256, lshm, st>>>(ctx->cells, l, npairs, in, o);
+            } else {
+                galerkin_tile_kernel<false><<<grid, 256, shm, st>>>(ctx->cells, l, npairs, in, o);
+            }
         }
         MLB_CHECK_LAUNCH(ctx, "galerkin_tile_kernel");
     }

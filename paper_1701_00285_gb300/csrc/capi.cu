@@ -217,6 +217,7 @@ mlb_status mlb_create(const mlb_opts* opts, mlb_ctx** out) {
         return MLB_ECUDA;
     }
     ctx->stream = ctx->own_stream;
+    cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, o.device);
     *out = ctx;
     return MLB_OK;
 }
@@ -338,6 +339,8 @@ static mlb_status build_basis_host(mlb_ctx* ctx, const double* pts, int64_t N, i
     ctx->gamma = (double*)dalloc(ctx, A, sizeof(double) * N);
     ctx->beta = (double*)dalloc(ctx, A, sizeof(double) * p);
     ctx->vec = (double*)dalloc(ctx, A, sizeof(double) * 10 * N);
+    ctx->ksum_part_cap = std::max<int64_t>(8 * N, 1 << 16);
+    ctx->ksum_part = (double*)dalloc(ctx, A, sizeof(double) * ctx->ksum_part_cap);
     ctx->partial = (double*)dalloc(ctx, A, sizeof(double) * (max_work_items(ncell, N) + 16384));
     ctx->pcg = (PcgState*)dalloc(ctx, A, sizeof(PcgState));
     CellTables& C = ctx->cells;
@@ -357,7 +360,7 @@ static mlb_status build_basis_host(mlb_ctx* ctx, const double* pts, int64_t N, i
     {
         const void* need[] = {ctx->xs, ctx->xs32, ctx->xl32, ctx->xs32lo, ctx->xl32lo, ctx->leafctr, ctx->perm, ctx->alpha, ctx->X, ctx->XtXf, ctx->V, ctx->R, ctx->sbuf,
                               ctx->flag, ctx->pan.rowCell, ctx->gW, ctx->gamma, ctx->beta, ctx->vec,
-                              ctx->partial, ctx->pcg, C.beg, C.end, C.s, C.a, C.k, C.vOff, C.rOff, C.wOff,
+                              ctx->partial, ctx->ksum_part, ctx->pcg, C.beg, C.end, C.s, C.a, C.k, C.vOff, C.rOff, C.wOff,
                               C.sOff, C.wLoc, C.lo, C.hi, C.diam};
         for (const void* q : need)
             if (!q) return fail(ctx, MLB_ENOMEM, ctx->err);

@@ -81,6 +81,9 @@ struct mlb_ctx {
     int state = 0;                 // 0 empty, 1 basis, 2 assembled, 3 solved
     int64_t launches = 0;          // kernels launched by this context
     int ksum_variant = 1;          // launch shape of the FP32 kernel sum (autotuned)
+    int nsm = 0;                   // SMs of the context's device
+    double* ksum_part = nullptr;   // kernel sums: partial sums of the source chunks
+    int64_t ksum_part_cap = 0;     // its length in doubles
 
     // basis
     int64_t N = 0, nwav = 0;

@@ -14,6 +14,12 @@
 // a cascaded FP32 sum (Sum2), the running sum over tiles in FP64.
 // Distances are formed from coordinate differences (no |x|^2 + |y|^2 - 2 x.y
 // cancellation).
+//
+// Source split: a grid of (target blocks) x (source chunks).  When there are
+// too few target blocks to fill the GPU, each CTA sums one chunk of the data
+// points and writes its partial sums to a work array; ksum_reduce_kernel adds
+// the chunks in order (FP64) and the trend.  With one chunk the kernels write
+// the result directly.
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -57,7 +63,8 @@ template <int D, bool DERIV>
 __global__ void __launch_bounds__(128) ksum_f64_kernel(const double* __restrict__ tg, int64_t M,
                                                        const double* __restrict__ xs,
                                                        const double* __restrict__ a, int64_t N, int kind,
-                                                       double scale, double* __restrict__ out, TrendArgs tr) {
+                                                       double scale, double* __restrict__ out, TrendArgs tr,
+                                                       int64_t jchunk, double* __restrict__ part) {
     __shared__ double sx[128 * D];
     __shared__ double sa[128];
     const int64_t k = blockIdx.x * 128LL + threadIdx.x;
@@ -65,8 +72,9 @@ __global__ void __launch_bounds__(128) ksum_f64_kernel(const double* __restrict_
 #pragma unroll
     for (int c = 0; c < D; ++c) y[c] = k < M ? tg[k * D + c] : 0.0;
     double acc = 0.0;
-    for (int64_t j0 = 0; j0 < N; j0 += 128) {
-        const int nj = (int)(N - j0 < 128 ? N - j0 : 128);
+    const int64_t jb = blockIdx.y * jchunk, je = min(N, jb + jchunk);
+    for (int64_t j0 = jb; j0 < je; j0 += 128) {
+        const int nj = (int)(je - j0 < 128 ? je - j0 : 128);
         __syncthreads();
         for (int idx = threadIdx.x; idx < nj * D; idx += 128) sx[idx] = xs[j0 * D + idx];
         if (threadIdx.x < nj) sa[threadIdx.x] = a[j0 + threadIdx.x];
@@ -83,6 +91,10 @@ __global__ void __launch_bounds__(128) ksum_f64_kernel(const double* __restrict_
         }
     }
     if (k >= M) return;
+    if (part) {
+        part[blockIdx.y * M + k] = acc;
+        return;
+    }
     if (tr.beta) add_trend<D>(acc, y, tr);
     out[k] = acc;
 }
@@ -94,7 +106,7 @@ __global__ void __launch_bounds__(BS) ksum_f32_kernel(const double* __restrict__
                                                        const double* __restrict__ src64,
                                                        const double* __restrict__ a, int64_t N, int kind,
                                                        float scale, Box3 ctr, double* __restrict__ out,
-                                                       TrendArgs tr) {
+                                                       TrendArgs tr, int64_t jchunk, double* __restrict__ part) {
     constexpr int TS = 256;
     __shared__ float sx[TS * D];
     __shared__ float sa[TS];      // weights split as a = a_hi + a_lo
@@ -109,8 +121,9 @@ __global__ void __launch_bounds__(BS) ksum_f32_kernel(const double* __restrict__
     double acc[TPT];
 #pragma unroll
     for (int t = 0; t < TPT; ++t) acc[t] = 0.0;
-    for (int64_t j0 = 0; j0 < N; j0 += TS) {
-        const int nj = (int)(N - j0 < TS ? N - j0 : TS);
+    const int64_t jb = blockIdx.y * jchunk, je = min(N, jb + jchunk);
+    for (int64_t j0 = jb; j0 < je; j0 += TS) {
+        const int nj = (int)(je - j0 < TS ? je - j0 : TS);
         __syncthreads();
         if (xs32) {
             for (int idx = threadIdx.x; idx < nj * D; idx += BS) sx[idx] = xs32[j0 * D + idx];
@@ -154,6 +167,10 @@ __global__ void __launch_bounds__(BS) ksum_f32_kernel(const double* __restrict__
     for (int t = 0; t < TPT; ++t) {
         const int64_t k = k0 + t;
         if (k >= M) continue;
+        if (part) {
+            part[blockIdx.y * M + k] = acc[t];
+            continue;
+        }
         double v = acc[t];
         if (tr.beta) {
             double yy[D];
@@ -177,7 +194,7 @@ __global__ void __launch_bounds__(128) ksum_ff_kernel(const double* __restrict__
                                                       const double* __restrict__ src64,
                                                       const double* __restrict__ a, int64_t N, int kind,
                                                       double scale, Box3 ctr, double* __restrict__ out,
-                                                      TrendArgs tr) {
+                                                      TrendArgs tr, int64_t jchunk, double* __restrict__ part) {
     constexpr int TS = 128;
     __shared__ float sxh[TS * D], sxl[TS * D];
     __shared__ float sah[TS], sal[TS];
@@ -194,8 +211,9 @@ __global__ void __launch_bounds__(128) ksum_ff_kernel(const double* __restrict__
     double acc[TPT];
 #pragma unroll
     for (int t = 0; t < TPT; ++t) acc[t] = 0.0;
-    for (int64_t j0 = 0; j0 < N; j0 += TS) {
-        const int nj = (int)(N - j0 < TS ? N - j0 : TS);
+    const int64_t jb = blockIdx.y * jchunk, je = min(N, jb + jchunk);
+    for (int64_t j0 = jb; j0 < je; j0 += TS) {
+        const int nj = (int)(je - j0 < TS ? je - j0 : TS);
         __syncthreads();
         if (xh32) {
             for (int idx = threadIdx.x; idx < nj * D; idx += 128) {
@@ -243,6 +261,10 @@ __global__ void __launch_bounds__(128) ksum_ff_kernel(const double* __restrict__
     for (int t = 0; t < TPT; ++t) {
         const int64_t kk = k0 + t;
         if (kk >= M) continue;
+        if (part) {
+            part[blockIdx.y * M + kk] = acc[t];
+            continue;
+        }
         double v = acc[t];
         if (tr.beta) {
             double yy[D];
@@ -252,6 +274,53 @@ __global__ void __launch_bounds__(128) ksum_ff_kernel(const double* __restrict__
         }
         out[kk] = v;
     }
+}
+
+// out_k = sum over chunks of part[chunk][k] (in chunk order) + trend
+template <int D>
+__global__ void __launch_bounds__(256) ksum_reduce_kernel(const double* __restrict__ part, int splits, int64_t M,
+                                                          const double* __restrict__ tg, double* __restrict__ out,
+                                                          TrendArgs tr) {
+    const int64_t k = blockIdx.x * 256LL + threadIdx.x;
+    if (k >= M) return;
+    double v = 0.0;
+    for (int c = 0; c < splits; ++c) v += part[c * M + k];
+    if (tr.beta) {
+        double yy[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) yy[c] = tg[k * D + c];
+        add_trend<D>(v, yy, tr);
+    }
+    out[k] = v;
+}
+
+// Source chunking for a grid of ctasM target blocks: about eight CTAs per SM in
+// all, every chunk at least four tiles of TS points, the partial sums within
+// the context's work array.  Returns the chunk length (a multiple of TS) and
+// the number of chunks; one chunk means no split.
+struct KsumSplit {
+    int64_t chunk;
+    int splits;
+};
+
+inline KsumSplit ksum_split(const mlb_ctx* ctx, int64_t ctasM, int64_t M, int64_t Ns, int TS) {
+    int64_t want = (8LL * ctx->nsm + ctasM - 1) / std::max<int64_t>(ctasM, 1);
+    want = std::min<int64_t>(want, Ns / (4LL * TS));
+    want = std::min<int64_t>(want, ctx->ksum_part_cap / std::max<int64_t>(M, 1));
+    want = std::min<int64_t>(want, 1024);
+    if (want <= 1 || !ctx->ksum_part) return {std::max<int64_t>(Ns, 1), 1};
+    int64_t chunk = (Ns + want - 1) / want;
+    chunk = (chunk + TS - 1) / TS * TS;
+    return {chunk, (int)((Ns + chunk - 1) / chunk)};
+}
+
+template <int D>
+static void launch_reduce(mlb_ctx* ctx, const KsumSplit& sp, const double* tg, int64_t M, double* out,
+                          const TrendArgs& tr) {
+    if (sp.splits <= 1) return;
+    ctx->launches += 1;     // the kernel sum's own launch is counted by its caller
+    ksum_reduce_kernel<D><<<(unsigned)((M + 255) / 256), 256, 0, ctx->stream>>>(ctx->ksum_part, sp.splits, M, tg,
+                                                                              out, tr);
 }
 
 // Launch shapes of the FP32 kernel sum (targets per thread x block size); the
@@ -264,28 +333,33 @@ constexpr int kVarBs[kKsumVariants] = {128, 128, 128, 256, 256, 256};
 constexpr bool tuned_dim(int D) { return D == 2 || D == 3 || D == 4 || D == 5 || D == 6 || D == 8 || D == 10; }
 
 template <int D, bool DERIV, int TPT, int BS>
-static void launch_f32_shape(cudaStream_t st, const double* tg, int64_t M, const float* xs32, const double* src,
+static void launch_f32_shape(mlb_ctx* ctx, const double* tg, int64_t M, const float* xs32, const double* src,
                              const double* a, int64_t Ns, int kind, float scale, const Box3& ctr, double* out,
                              const TrendArgs& tr) {
-    const unsigned grid = (unsigned)((M + (int64_t)BS * TPT - 1) / ((int64_t)BS * TPT));
-    ksum_f32_kernel<D, TPT, DERIV, BS><<<grid, BS, 0, st>>>(tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr);
+    const int64_t ctasM = (M + (int64_t)BS * TPT - 1) / ((int64_t)BS * TPT);
+    const KsumSplit sp = ksum_split(ctx, ctasM, M, Ns, 256);
+    const dim3 grid((unsigned)ctasM, (unsigned)sp.splits);
+    ksum_f32_kernel<D, TPT, DERIV, BS><<<grid, BS, 0, ctx->stream>>>(tg, M, xs32, src, a, Ns, kind, scale, ctr, out,
+                                                                     tr, sp.chunk,
+                                                                     sp.splits > 1 ? ctx->ksum_part : nullptr);
+    launch_reduce<D>(ctx, sp, tg, M, out, tr);
 }
 
 template <int D, bool DERIV>
-static void launch_f32_variant(int v, cudaStream_t st, const double* tg, int64_t M, const float* xs32,
+static void launch_f32_variant(int v, mlb_ctx* ctx, const double* tg, int64_t M, const float* xs32,
                                const double* src, const double* a, int64_t Ns, int kind, float scale,
                                const Box3& ctr, double* out, const TrendArgs& tr) {
     if constexpr (tuned_dim(D) && !DERIV) {
         switch (v) {
-            case 0: launch_f32_shape<D, DERIV, 2, 128>(st, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
-            case 2: launch_f32_shape<D, DERIV, 8, 128>(st, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
-            case 3: launch_f32_shape<D, DERIV, 2, 256>(st, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
-            case 4: launch_f32_shape<D, DERIV, 4, 256>(st, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
-            case 5: launch_f32_shape<D, DERIV, 8, 256>(st, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
+            case 0: launch_f32_shape<D, DERIV, 2, 128>(ctx, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
+            case 2: launch_f32_shape<D, DERIV, 8, 128>(ctx, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
+            case 3: launch_f32_shape<D, DERIV, 2, 256>(ctx, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
+            case 4: launch_f32_shape<D, DERIV, 4, 256>(ctx, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
+            case 5: launch_f32_shape<D, DERIV, 8, 256>(ctx, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
             default: break;
         }
     }
-    launch_f32_shape<D, DERIV, 4, 128>(st, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr);
+    launch_f32_shape<D, DERIV, 4, 128>(ctx, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr);
 }
 
 template <int D, bool DERIV>
@@ -297,21 +371,26 @@ static void launch_ksum(mlb_ctx* ctx, const double* tg, int64_t M, const double*
         Box3 ctr;
         for (int c = 0; c < kMaxDim; ++c) ctr.c[c] = c < ctx->d ? 0.5 * (ctx->box_lo[c] + ctx->box_hi[c]) : 0.0;
         constexpr int TPT = 2;
-        const unsigned grid = (unsigned)((M + 128 * TPT - 1) / (128 * TPT));
-        ksum_ff_kernel<D, TPT, DERIV><<<grid, 128, 0, ctx->stream>>>(
-            tg, M, src ? nullptr : ctx->xs32, src ? nullptr : ctx->xs32lo, src, a, Ns, kind, scale, ctr, out, tr);
+        const int64_t ctasM = (M + 128 * TPT - 1) / (128 * TPT);
+        const KsumSplit sp = ksum_split(ctx, ctasM, M, Ns, 128);
+        ksum_ff_kernel<D, TPT, DERIV><<<dim3((unsigned)ctasM, (unsigned)sp.splits), 128, 0, ctx->stream>>>(
+            tg, M, src ? nullptr : ctx->xs32, src ? nullptr : ctx->xs32lo, src, a, Ns, kind, scale, ctr, out, tr,
+            sp.chunk, sp.splits > 1 ? ctx->ksum_part : nullptr);
+        launch_reduce<D>(ctx, sp, tg, M, out, tr);
         return;
     }
     if (ctx->opts.precision == MLB_MIXED) {
         Box3 ctr;
         for (int c = 0; c < kMaxDim; ++c) ctr.c[c] = c < ctx->d ? 0.5 * (ctx->box_lo[c] + ctx->box_hi[c]) : 0.0;
-        launch_f32_variant<D, DERIV>(DERIV ? 1 : ctx->ksum_variant, ctx->stream, tg, M, src ? nullptr : ctx->xs32, src,
+        launch_f32_variant<D, DERIV>(DERIV ? 1 : ctx->ksum_variant, ctx, tg, M, src ? nullptr : ctx->xs32, src,
                                      a, Ns, kind, (float)scale, ctr, out, tr);
         return;
     }
-    const unsigned grid = (unsigned)((M + 127) / 128);
-    ksum_f64_kernel<D, DERIV><<<grid, 128, 0, ctx->stream>>>(tg, M, src ? src : ctx->xs, a, Ns, kind, scale,
-                                                              out, tr);
+    const int64_t ctasM = (M + 127) / 128;
+    const KsumSplit sp = ksum_split(ctx, ctasM, M, Ns, 128);
+    ksum_f64_kernel<D, DERIV><<<dim3((unsigned)ctasM, (unsigned)sp.splits), 128, 0, ctx->stream>>>(
+        tg, M, src ? src : ctx->xs, a, Ns, kind, scale, out, tr, sp.chunk, sp.splits > 1 ? ctx->ksum_part : nullptr);
+    launch_reduce<D>(ctx, sp, tg, M, out, tr);
 }
 
 

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) spmv_panel_kernel(Panels pan, const T* __
 // current chunk is multiplied and stored after it, so one barrier per chunk
 // remains and the gather hides behind the value stream.  Products in FP32,
 // each row's chunk sums in a cascaded FP32 sum (Sum2), the reduction in FP64.
-__global__ void __launch_bounds__(256) spmv_panel_f32_kernel(Panels pan, const float* __restrict__ vals,
+__global__ void __launch_bounds__(256, 4) spmv_panel_f32_kernel(Panels pan, const float* __restrict__ vals,
                                                              const int* __restrict__ kcell,
                                                              const int64_t* __restrict__ wOff,
                                                              const double* __restrict__ x, double* __restrict__ y,

@@ -4,9 +4,13 @@ Builds the multilevel basis and assembles C~_W for a seeded dense-pattern
 problem (all level pairs admissible, tau = infinity), then times
 ``mlb_cw_matvec_dev`` on the device with CUDA events on the context's stream.
 The panels are larger than the L2 cache at the default size, so every call
-streams them from HBM.  One JSON line per precision:
+streams them from HBM.  With ``--matrix-free`` the product is the three-step
+W (C (W^T u)) + eta u whose middle step is an N x N kernel sum (the
+high-dimensional workload: 262,144 points in [0,1]^10, nu = 5/2, w = 2, leaf
+128).  One JSON line per precision:
 
     python -m paper_1701_00285_gb300.matvec_bench --n 32768 --precision mixed --reps 20
+    python -m paper_1701_00285_gb300.matvec_bench --matrix-free --n 262144 --precision mixed --reps 3
 """
 from __future__ import annotations
 
@@ -21,20 +25,22 @@ def main(argv=None) -> None:
     ap.add_argument("--precision", default="mixed,fp64", help="comma list of mixed, fp64")
     ap.add_argument("--reps", type=int, default=20, help="timed products")
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--leaf-size", type=int, default=64)
+    ap.add_argument("--leaf-size", type=int, default=None, help="default: the workload's leaf size")
+    ap.add_argument("--matrix-free", action="store_true", help="d = 10 three-step product")
     a = ap.parse_args(argv)
 
     import torch
     import workloads as wl
     from .binding import Context
 
-    P = wl.config5(N=a.n, M=512)
+    P = wl.config3(N=a.n, M=512) if a.matrix_free else wl.config5(N=a.n, M=512)
+    leaf = a.leaf_size or P.leaf_size
     st = torch.cuda.Stream()
     for prec in a.precision.split(","):
-        c = Context(prec, leaf_size=a.leaf_size)
+        c = Context(prec, leaf_size=leaf, matrix_free=a.matrix_free)
         try:
             c.set_stream(st.cuda_stream)
-            c.build_basis(P.points, 1)
+            c.build_basis(P.points, P.w)
             c.assemble(P.nu, P.rho, P.nugget, math.inf)
             nw = c.nwav
             with torch.cuda.stream(st):
@@ -52,13 +58,20 @@ def main(argv=None) -> None:
             e1.record(st)
             e1.synchronize()
             ms = e0.elapsed_time(e1) / max(a.reps, 1)
-            vb = 4 if prec == "mixed" else 8
-            # tau = infinity makes the pattern dense: nwav^2 entries.  Algorithmic
-            # bytes: every entry once, u read and C~_W u written.
-            nnz = nw * nw
-            algo = nnz * vb + 2 * nw * 8
-            print(json.dumps({"precision": prec, "n": a.n, "nwav": nw, "nnz": nnz, "ms": ms,
-                              "algorithmic_bytes": algo, "GBps": algo / ms / 1e6}), flush=True)
+            if a.matrix_free:
+                # the kernel sum dominates: N^2 point pairs per product
+                pairs = a.n * a.n
+                print(json.dumps({"precision": prec, "n": a.n, "d": P.points.shape[1], "nwav": nw,
+                                  "matrix_free": True, "ms": ms, "pairs": pairs,
+                                  "pairs_per_s": pairs / (ms / 1000.0)}), flush=True)
+            else:
+                vb = 4 if prec == "mixed" else 8
+                # tau = infinity makes the pattern dense: nwav^2 entries.  Algorithmic
+                # bytes: every entry once, u read and C~_W u written.
+                nnz = nw * nw
+                algo = nnz * vb + 2 * nw * 8
+                print(json.dumps({"precision": prec, "n": a.n, "nwav": nw, "nnz": nnz, "ms": ms,
+                                  "algorithmic_bytes": algo, "GBps": algo / ms / 1e6}), flush=True)
         finally:
             c.close()
 
