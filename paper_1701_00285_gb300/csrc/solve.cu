@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(256) spmv_panel_kernel(Panels pan, const T* __
 // current chunk is multiplied and stored after it, so one barrier per chunk
 // remains and the gather hides behind the value stream.  Products in FP32,
 // each row's chunk sums in a cascaded FP32 sum (Sum2), the reduction in FP64.
+// 64 registers, so four CTAs (32 warps) stay resident per SM.
 __global__ void __launch_bounds__(256, 4) spmv_panel_f32_kernel(Panels pan, const float* __restrict__ vals,
                                                              const int* __restrict__ kcell,
                                                              const int64_t* __restrict__ wOff,
@@ -205,6 +206,15 @@ __global__ void __launch_bounds__(256, 4) spmv_panel_f32_kernel(Panels pan, cons
     for (int c0 = 0; c0 < n; c0 += CH) {
         const int m = min(CH, n - c0);
         const int cn = c0 + CH + threadIdx.x;
+        // one thread per row asks the L2 for the row's next chunk (a bulk
+        // prefetch, no registers held), so HBM streams it while this chunk's
+        // loads and products run.  Rows start 16-byte aligned and the chunk
+        // length is a multiple of 4 values, as the bulk copy requires.
+        const int pc = c0 + CH;
+        if (threadIdx.x < rows && pc < n)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(v0 + (int64_t)threadIdx.x * nn + pc),
+                         "r"((unsigned)(min(CH, n - pc) * 4))
+                         : "memory");
         const double xn = cn < n ? x[ci[cn]] : 0.0;
         const float* sh = xh[buf];
         const float* sl = xl[buf];
@@ -299,13 +309,18 @@ __global__ void pcg_init_kernel(int64_t n, const double* __restrict__ b, const d
     }
 }
 
-__global__ void pcg_init_scalars(const double* part, PcgState* st) {
-    if (threadIdx.x) return;
-    double rz = 0.0, bb = 0.0;
-    for (int i = 0; i < kVecBlocks; ++i) {
-        rz += part[i];
-        bb += part[kVecBlocks + i];
+// The scalar kernels reduce the per-block partial sums with one CTA (strided
+// per-thread sums, then a fixed-order tree), so their results are
+// deterministic and they do not serialise on one thread's loads.
+__global__ void __launch_bounds__(256) pcg_init_scalars(const double* part, PcgState* st) {
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < kVecBlocks; i += blockDim.x) {
+        a += part[i];
+        b += part[kVecBlocks + i];
     }
+    const double rz = block_reduce(a);
+    const double bb = block_reduce(b);
+    if (threadIdx.x) return;
     st->rz = rz;
     st->bb = bb;
     st->rr = bb;
@@ -314,10 +329,12 @@ __global__ void pcg_init_scalars(const double* part, PcgState* st) {
     st->done = bb == 0.0 ? 1 : 0;
 }
 
-__global__ void pcg_alpha_kernel(const double* part, int nparts, PcgState* st) {
-    if (threadIdx.x || st->done) return;
-    double pq = 0.0;
-    for (int i = 0; i < nparts; ++i) pq += part[i];
+__global__ void __launch_bounds__(256) pcg_alpha_kernel(const double* part, int nparts, PcgState* st) {
+    if (st->done) return;
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) a += part[i];
+    const double pq = block_reduce(a);
+    if (threadIdx.x) return;
     st->pq = pq;
     if (!(pq > 0.0)) {
         st->status = ST_BREAKDOWN;
@@ -350,13 +367,16 @@ __global__ void pcg_update_xr_kernel(int64_t n, const PcgState* st, const double
     }
 }
 
-__global__ void pcg_beta_kernel(const double* part, PcgState* st, double tol2, int maxit) {
-    if (threadIdx.x || st->done) return;
-    double rr = 0.0, rz = 0.0;
-    for (int i = 0; i < kVecBlocks; ++i) {
-        rr += part[i];
-        rz += part[kVecBlocks + i];
+__global__ void __launch_bounds__(256) pcg_beta_kernel(const double* part, PcgState* st, double tol2, int maxit) {
+    if (st->done) return;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < kVecBlocks; i += blockDim.x) {
+        a += part[i];
+        b += part[kVecBlocks + i];
     }
+    const double rr = block_reduce(a);
+    const double rz = block_reduce(b);
+    if (threadIdx.x) return;
     st->it += 1;
     st->rr = rr;
     st->beta = rz / st->rz;
@@ -468,15 +488,15 @@ static mlb_status launch_iteration(mlb_ctx* ctx, double* x, double* r, double* z
         // converged, the kernels that check the flag return at once
         mlb_status s = three_step(ctx, p, q, ctx->partial, ctx->pcg);
         if (s != MLB_OK) return s;
-        pcg_alpha_kernel<<<1, 32, 0, st>>>(ctx->partial, kVecBlocks, ctx->pcg);
+        pcg_alpha_kernel<<<1, 256, 0, st>>>(ctx->partial, kVecBlocks, ctx->pcg);
     } else {
         launch_spmv(ctx, p, q, ctx->partial, ctx->pcg);
         ctx->launches += 1;
-        pcg_alpha_kernel<<<1, 32, 0, st>>>(ctx->partial, ctx->pan.vals32 ? std::max(ctx->pan.nwork, 1) : ctx->ncell,
+        pcg_alpha_kernel<<<1, 256, 0, st>>>(ctx->partial, ctx->pan.vals32 ? std::max(ctx->pan.nwork, 1) : ctx->ncell,
                                            ctx->pcg);
     }
     pcg_update_xr_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, p, q, diag, x, r, z, part2);
-    pcg_beta_kernel<<<1, 32, 0, st>>>(part2, ctx->pcg, tol2, ctx->opts.pcg_maxit);
+    pcg_beta_kernel<<<1, 256, 0, st>>>(part2, ctx->pcg, tol2, ctx->opts.pcg_maxit);
     pcg_update_p_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, z, p);
     ctx->launches += 4;
     return MLB_OK;
@@ -493,7 +513,7 @@ mlb_status pcg_run(mlb_ctx* ctx, const double* b, double* x, mlb_info* info) {
     double* q = ctx->vec + 4 * n;
     const double* diag = ctx->opts.precond ? ctx->diag : nullptr;
     pcg_init_kernel<<<kVecBlocks, 256, 0, st>>>(n, b, diag, x, r, z, p, ctx->partial);
-    pcg_init_scalars<<<1, 32, 0, st>>>(ctx->partial, ctx->pcg);
+    pcg_init_scalars<<<1, 256, 0, st>>>(ctx->partial, ctx->pcg);
     MLB_CHECK_LAUNCH(ctx, "pcg_init");
     ctx->launches += 1;
     const double tol2 = ctx->opts.pcg_rtol * ctx->opts.pcg_rtol;
