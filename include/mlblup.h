@@ -181,6 +181,10 @@ mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* probs, int c
                            double* ms_out);
 /* Message of the last failing mlb_batch_solve on the calling thread ("" if none). */
 const char* mlb_batch_last_error(void);
+/* Wall-clock milliseconds of the last mlb_batch_solve on the calling thread,
+ * by phase: [0] setup (basis, assembly, Z_W), [1] PCG, [2] closing (gamma,
+ * trend, predictions, context release).  out: 3 doubles (host). */
+void mlb_batch_last_phase_ms(double* out);
 
 /* ---- inspection (tests and tools) ---------------------------------------- */
 

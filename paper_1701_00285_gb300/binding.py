@@ -76,6 +76,7 @@ _SIGS = {
     "mlb_batch_solve": (ctypes.c_int, [ctypes.POINTER(Opts), ctypes.POINTER(BatchProblem), ctypes.c_int,
                                        ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "mlb_batch_last_error": (ctypes.c_char_p, []),
+    "mlb_batch_last_phase_ms": (None, [ctypes.POINTER(ctypes.c_double)]),
     "mlb_get_sizes": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(_I64)]),
@@ -155,6 +156,13 @@ def batch_solve(problems, precision: str = "fp64", leaf_size: int = 64, pcg_rtol
         import warnings
         warnings.warn("mlb_batch_solve: " + L.mlb_batch_last_error().decode())
     return res, ms.value, st
+
+
+def batch_last_phase_ms() -> dict:
+    """Per-phase wall-clock ms of the calling thread's last batch_solve."""
+    out = (ctypes.c_double * 3)()
+    lib().mlb_batch_last_phase_ms(out)
+    return {"setup": out[0], "pcg": out[1], "finish": out[2]}
 
 
 class Context:

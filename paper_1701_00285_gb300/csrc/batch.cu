@@ -9,7 +9,10 @@
 // launches per iteration on systems of a few thousand unknowns), is one
 // persistent launch: one CTA per problem runs its whole diagonally
 // preconditioned CG (Sec. 5.2 remark, Sec. 6.2) with block-level reductions
-// only -- no CTA waits for another.
+// only -- no CTA waits for another.  Problems with more than kCtaRows
+// unknowns would hold one SM for many iterations of a product that wants
+// the whole GPU; they run the single-problem PCG (full-grid product, CUDA
+// graph chunks) on the stream pool while the persistent launch runs.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -21,6 +24,9 @@
 #include "internal.h"
 
 namespace mlb {
+
+// largest system solved by one CTA of the persistent launch
+constexpr int kCtaRows = 1024;
 
 struct BatchPcgProblem {
     const double* vals64;      // panel values (FP64 path) or nullptr
@@ -57,10 +63,16 @@ __device__ double cta_sum(double v, double* red) {
     return s;
 }
 
-// q = A p by warp-per-row over the problem's panels; returns p.q (all threads)
+// q = A p by warp-per-row over the problem's panels; returns p.q (all
+// threads).  p is staged in shared memory first (n <= kCtaRows), so the
+// column gather reads shared memory and only the values and column indices
+// stream from global memory, four at a time (panel rows start 16-byte
+// aligned and hold a multiple of 4 columns).
 __device__ double cta_spmv(const BatchPcgProblem& P, const double* __restrict__ pv, double* __restrict__ q,
-                           double* red) {
+                           double* xs, double* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t i = threadIdx.x; i < P.n; i += blockDim.x) xs[i] = pv[i];
+    __syncthreads();
     double dot = 0.0;
     for (int64_t r = warp; r < P.n; r += nw) {
         const int g = P.rowCell[r];
@@ -70,15 +82,24 @@ __device__ double cta_spmv(const BatchPcgProblem& P, const double* __restrict__ 
         double acc = 0.0;
         if (P.vals32) {
             const float* v = P.vals32 + P.valOff[g] + i * n;
-            for (int j = lane; j < n; j += 32) acc += (double)v[j] * pv[ci[j]];
+            for (int j = 4 * lane; j < n; j += 128) {
+                const float4 a = *reinterpret_cast<const float4*>(v + j);
+                const int4 c = *reinterpret_cast<const int4*>(ci + j);
+                acc += (double)a.x * xs[c.x] + (double)a.y * xs[c.y] + (double)a.z * xs[c.z] + (double)a.w * xs[c.w];
+            }
         } else {
             const double* v = P.vals64 + P.valOff[g] + i * n;
-            for (int j = lane; j < n; j += 32) acc += v[j] * pv[ci[j]];
+            for (int j = 4 * lane; j < n; j += 128) {
+                const double2 a = *reinterpret_cast<const double2*>(v + j);
+                const double2 b = *reinterpret_cast<const double2*>(v + j + 2);
+                const int4 c = *reinterpret_cast<const int4*>(ci + j);
+                acc += a.x * xs[c.x] + a.y * xs[c.y] + b.x * xs[c.z] + b.y * xs[c.w];
+            }
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) {
             q[r] = acc;
-            dot += pv[r] * acc;
+            dot += xs[r] * acc;
         }
     }
     return cta_sum(dot, red);
@@ -88,6 +109,7 @@ __device__ double cta_spmv(const BatchPcgProblem& P, const double* __restrict__ 
 // ||r_k||^2 <= tol^2 ||b||^2 on the recursive unpreconditioned residual.
 __global__ void __launch_bounds__(512) batch_pcg_kernel(const BatchPcgProblem* __restrict__ probs) {
     __shared__ double red[32];
+    __shared__ double xs[kCtaRows];
     const BatchPcgProblem P = probs[blockIdx.x];
     const int64_t n = P.n;
     double rz = 0.0, bb = 0.0;
@@ -108,7 +130,7 @@ __global__ void __launch_bounds__(512) batch_pcg_kernel(const BatchPcgProblem* _
     if (bb > 0.0) {
         while (true) {
             __syncthreads();
-            const double pq = cta_spmv(P, P.p, P.q, red);
+            const double pq = cta_spmv(P, P.p, P.q, xs, red);
             if (!(pq > 0.0)) {
                 status = 1;
                 break;
@@ -153,6 +175,11 @@ using namespace mlb;
 namespace {
 
 thread_local std::string g_batch_err;
+thread_local double g_batch_phase_ms[3] = {0.0, 0.0, 0.0};
+
+double ms_since(std::chrono::steady_clock::time_point t) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+}
 
 struct Job {
     mlb_batch_problem* prob;
@@ -201,6 +228,21 @@ mlb_status finish_one(Job& j) {
     return MLB_OK;
 }
 
+// f(job, thread) over the listed jobs that are still OK, on `threads` host threads
+template <typename F>
+void run_listed(std::vector<Job>& jobs, const std::vector<int>& list, int threads, F f) {
+    std::atomic<int> next(0);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < threads; ++t)
+        pool.emplace_back([&, t]() {
+            for (int k = next.fetch_add(1); k < (int)list.size(); k = next.fetch_add(1)) {
+                Job& j = jobs[list[k]];
+                if (j.status == MLB_OK) j.status = f(j, t);
+            }
+        });
+    for (auto& th : pool) th.join();
+}
+
 template <typename F>
 void run_parallel(std::vector<Job>& jobs, int threads, F f) {
     std::atomic<int> next(0);
@@ -216,6 +258,11 @@ void run_parallel(std::vector<Job>& jobs, int threads, F f) {
 }  // namespace
 
 extern "C" const char* mlb_batch_last_error(void) { return g_batch_err.c_str(); }
+
+extern "C" void mlb_batch_last_phase_ms(double* out) {
+    if (out)
+        for (int i = 0; i < 3; ++i) out[i] = g_batch_phase_ms[i];
+}
 
 extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* probs, int count, int host_threads,
                                       double* ms_out) {
@@ -238,16 +285,24 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
         probs[i].iterations = 0;
     }
     // phase 1: basis, assembly, Z_W
+    for (double& v : g_batch_phase_ms) v = 0.0;
+    auto tp = std::chrono::steady_clock::now();
     run_parallel(jobs, threads, [&](Job& j, int t) {
         cudaSetDevice(o.device);
         return setup_one(j, o, streams[t]);
     });
     for (auto& s : streams) cudaStreamSynchronize(s);
-    // phase 2: all PCG solves in one launch
+    g_batch_phase_ms[0] = ms_since(tp);
+    tp = std::chrono::steady_clock::now();
+    // phase 2: the small systems in one persistent launch (largest first, so
+    // the longest CTAs start first), the large ones on the stream pool
+    std::vector<int> order, big;
+    for (int i = 0; i < count; ++i)
+        if (jobs[i].status == MLB_OK) (jobs[i].ctx->nwav > kCtaRows ? big : order).push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].ctx->nwav > jobs[b].ctx->nwav; });
     std::vector<BatchPcgProblem> hp;
     std::vector<int> idx;
-    for (int i = 0; i < count; ++i) {
-        if (jobs[i].status != MLB_OK) continue;
+    for (int i : order) {
         mlb_ctx* c = jobs[i].ctx;
         BatchPcgProblem b{};
         b.vals64 = c->pan.vals32 ? nullptr : c->pan.vals;
@@ -273,26 +328,49 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
         idx.push_back(i);
     }
     mlb_status first = MLB_OK;
+    BatchPcgProblem* dp = nullptr;
+    cudaStream_t ps = nullptr;
     if (!hp.empty()) {
-        BatchPcgProblem* dp = nullptr;
-        if (cudaMalloc(&dp, sizeof(BatchPcgProblem) * hp.size()) != cudaSuccess) {
+        if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMalloc(&dp, sizeof(BatchPcgProblem) * hp.size()) != cudaSuccess) {
             first = MLB_ENOMEM;
-            g_batch_err = "cudaMalloc of the problem table failed";
+            g_batch_err = "stream or problem table for the persistent PCG";
         }
         if (first == MLB_OK) {
-            cudaMemcpy(dp, hp.data(), sizeof(BatchPcgProblem) * hp.size(), cudaMemcpyHostToDevice);
-            batch_pcg_kernel<<<(unsigned)hp.size(), 512>>>(dp);
-            cudaError_t e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            cudaError_t e = cudaMemcpyAsync(dp, hp.data(), sizeof(BatchPcgProblem) * hp.size(),
+                                            cudaMemcpyHostToDevice, ps);
+            if (e == cudaSuccess) {
+                batch_pcg_kernel<<<(unsigned)hp.size(), 512, 0, ps>>>(dp);
+                e = cudaGetLastError();
+            }
             if (e != cudaSuccess) {
                 first = MLB_ECUDA;
                 g_batch_err = std::string("batch_pcg_kernel: ") + cudaGetErrorString(e);
             }
-            cudaFree(dp);
         }
-        if (first == MLB_OK)
-            for (int i : idx) jobs[i].ctx->launches += 1;
     }
+    if (first == MLB_OK && !big.empty())
+        run_listed(jobs, big, threads, [&](Job& j, int t) {
+            cudaSetDevice(o.device);
+            mlb_set_stream(j.ctx, streams[t]);
+            mlb_info inf{};
+            const mlb_status s = pcg_run(j.ctx, j.ctx->vec, j.ctx->gW, &inf);
+            // breakdown and non-convergence are reported per problem by finish_one
+            return (s == MLB_EBREAKDOWN || s == MLB_ENOCONV) ? MLB_OK : s;
+        });
+    if (ps) {
+        const cudaError_t e = cudaStreamSynchronize(ps);
+        if (e != cudaSuccess && first == MLB_OK) {
+            first = MLB_ECUDA;
+            g_batch_err = std::string("batch_pcg_kernel: ") + cudaGetErrorString(e);
+        }
+        cudaStreamDestroy(ps);
+    }
+    if (dp) cudaFree(dp);
+    if (first == MLB_OK)
+        for (int i : idx) jobs[i].ctx->launches += 1;
+    g_batch_phase_ms[1] = ms_since(tp);
+    tp = std::chrono::steady_clock::now();
     // phase 3: gamma, trend, predictions
     if (first == MLB_OK)
         run_parallel(jobs, threads, [&](Job& j, int) {
@@ -308,6 +386,7 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
         if (jobs[i].ctx) mlb_destroy(jobs[i].ctx);
     }
     for (auto& s : streams) cudaStreamDestroy(s);
+    g_batch_phase_ms[2] = ms_since(tp);
     if (ms_out)
         *ms_out = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return first;

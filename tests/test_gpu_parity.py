@@ -7,6 +7,7 @@ basis chosen inside each cell), gamma-hat, beta-hat and the predictions.
 Tolerances: FP64 path 1e-9 relative on predictions (1e-12 on the operators),
 PCG run to 1e-13 on both sides.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -360,9 +361,10 @@ def test_high_dimension_subsample_matrix_free(pkg):
 
 def test_batched_problems_mixed_vs_oracle(pkg):
     """Problems drawn from the batched workload's generator (d in {2,3,5}, all
-    three nu, rho in [0.1, 0.5], tau = 2 diameters), both precisions vs the
-    multilevel oracle's exact solve of the same truncated system."""
-    probs = [q for q in wl.config4(count=60) if q.N <= 1400][:4]
+    three nu, rho in [0.1, 0.5]) truncated at tau = 2 diameters, both
+    precisions vs the multilevel oracle's exact solve of the same truncated
+    system."""
+    probs = [dataclasses.replace(q, tau_factor=2.0) for q in wl.config4(count=60) if q.N <= 1400][:4]
     assert len(probs) == 4
     for P in probs:
         B = mlblup.setup(P.points, P.w, P.leaf_size)
@@ -398,7 +400,7 @@ def test_batch_solve_matches_oracle(pkg, prec, tol):
     tau = 2 diameters) through mlb_batch_solve, each against the multilevel
     oracle's exact solve of its own truncated system."""
     from paper_1701_00285_gb300.binding import batch_solve
-    probs = [q for q in wl.config4(count=80) if q.N <= 1500][:6]
+    probs = [dataclasses.replace(q, tau_factor=2.0) for q in wl.config4(count=80) if q.N <= 1500][:6]
     items = [{"points": q.points, "w": q.w, "nu": q.nu, "rho": q.rho, "nugget": q.nugget,
               "tau_factor": q.tau_factor, "Z": q.Z, "targets": q.targets[:150]} for q in probs]
     res, ms, st = batch_solve(items, precision=prec, pcg_rtol=1e-12, pcg_maxit=50000)
@@ -411,3 +413,24 @@ def test_batch_solve_matches_oracle(pkg, prec, tol):
         yref = mlblup.predict(B, q.points, g, bb, q.targets[:150], q.nu, q.rho)
         assert rel(y, yref) < tol, q.name
         assert rel(b, bb) < 1e3 * tol, q.name
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", MIXED_TOL)])
+def test_batch_solve_mixed_sizes_dense_oracle(pkg, prec, tol):
+    """A batch with systems on both sides of the persistent-launch size limit
+    (1,024 unknowns): the small ones run one CTA each, the large one the
+    full-grid PCG on the stream pool.  tau = infinity, so each must equal the
+    dense BLUP of its own data."""
+    from paper_1701_00285_gb300.binding import batch_solve
+    small = [q for q in wl.config4(count=40) if q.N <= 1000][:2]
+    big = wl.small_problem(590, 2600, 3, 1, nu=1.5, rho=0.3, nugget=1e-4, leaf_size=64, M=150)
+    probs = small + [big]
+    items = [{"points": q.points, "w": q.w, "nu": q.nu, "rho": q.rho, "nugget": q.nugget,
+              "tau_factor": math.inf, "Z": q.Z, "targets": q.targets[:150]} for q in probs]
+    res, ms, st = batch_solve(items, precision=prec, pcg_rtol=1e-12, pcg_maxit=50000)
+    from paper_1701_00285_gb300 import lib
+    assert st == 0, lib().mlb_batch_last_error().decode()
+    for q, (y, b, s, its) in zip(probs, res):
+        assert s == 0 and its > 0, q.name
+        ref = dense.dense_blup(q.points, q.Z, q.targets[:150], q.w, q.nu, q.rho, q.nugget)
+        assert rel(y, ref["yhat"]) < tol, (q.name, prec)
