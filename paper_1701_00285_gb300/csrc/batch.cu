@@ -81,11 +81,26 @@ __device__ double cta_spmv(const BatchPcgProblem& P, const double* __restrict__ 
         const int* ci = P.colidx + P.colOff[g];
         double acc = 0.0;
         if (P.vals32) {
+            // four 16-byte value and index loads per lane in flight before any is used
             const float* v = P.vals32 + P.valOff[g] + i * n;
-            for (int j = 4 * lane; j < n; j += 128) {
-                const float4 a = *reinterpret_cast<const float4*>(v + j);
-                const int4 c = *reinterpret_cast<const int4*>(ci + j);
-                acc += (double)a.x * xs[c.x] + (double)a.y * xs[c.y] + (double)a.z * xs[c.z] + (double)a.w * xs[c.w];
+            for (int j0 = 4 * lane; j0 < n; j0 += 512) {
+                float4 a[4];
+                int4 c[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + 128 * u;
+                    if (j < n) {
+                        a[u] = *reinterpret_cast<const float4*>(v + j);
+                        c[u] = *reinterpret_cast<const int4*>(ci + j);
+                    } else {
+                        a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        c[u] = make_int4(0, 0, 0, 0);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    acc += (double)a[u].x * xs[c[u].x] + (double)a[u].y * xs[c[u].y] + (double)a[u].z * xs[c[u].z] +
+                           (double)a[u].w * xs[c[u].w];
             }
         } else {
             const double* v = P.vals64 + P.valOff[g] + i * n;

@@ -63,7 +63,8 @@ inline size_t max_work_items(int ncell, int64_t N) { return (size_t)ncell + (siz
 
 struct PcgState {
     double rz, rr, bb, alpha, beta, pq;
-    int it, done, status, pad;
+    int it, done, status;
+    unsigned ticket;     // CTAs of the current launch that have finished (last-CTA reductions)
 };
 
 struct Arena {

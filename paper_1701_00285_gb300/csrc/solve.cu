@@ -19,6 +19,7 @@
 namespace mlb {
 
 constexpr int kVecBlocks = 512;
+constexpr int64_t kFusePMax = 16384;   // longest vector whose p update the last CTA does
 
 enum { ST_OK = 0, ST_BREAKDOWN = 1, ST_NOCONV = 2 };
 
@@ -35,6 +36,38 @@ __device__ double block_reduce(double v) {
     }
     __syncthreads();
     return s;   // valid in thread 0
+}
+
+// Last-CTA reduction: every CTA of a launch has written its partial sums;
+// each then draws a ticket, and the CTA that draws the last one (after a
+// fence, so it sees every partial) finishes the reduction in a fixed order.
+// No CTA waits for another.  The ticket is reset for the next launch.
+__device__ bool draw_last_ticket(PcgState* st) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+        if (last) st->ticket = 0;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// alpha = (r.z) / (p.q) from the per-CTA partials of p.q
+__device__ void pcg_alpha_finish(const double* part, int nparts, PcgState* st) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) a += __ldcg(part + i);
+    const double pq = block_reduce(a);
+    if (threadIdx.x) return;
+    st->pq = pq;
+    if (!(pq > 0.0)) {
+        st->status = ST_BREAKDOWN;
+        st->done = 1;
+        return;
+    }
+    st->alpha = st->rz / pq;
 }
 
 // y = A x over the row panels, one CTA per panel (heaviest panels first).
@@ -63,7 +96,7 @@ __global__ void __launch_bounds__(256) spmv_panel_kernel(Panels pan, const T* __
                                                          const int* __restrict__ kcell,
                                                          const int64_t* __restrict__ wOff, int ncell,
                                                          const double* __restrict__ x, double* __restrict__ y,
-                                                         double* __restrict__ part, const PcgState* st) {
+                                                         double* __restrict__ part, PcgState* st) {
     if (st && st->done) return;
     using V2 = typename Vec2<T>::type;
     constexpr int CH = 256;
@@ -159,6 +192,8 @@ __global__ void __launch_bounds__(256) spmv_panel_kernel(Panels pan, const T* __
             for (int i = 0; i < 8; ++i) s2 += red[i];
             part[blockIdx.x] = s2;
         }
+        // inside the PCG the last CTA also forms alpha
+        if (st && draw_last_ticket(st)) pcg_alpha_finish(part, gridDim.x, st);
     }
 }
 
@@ -176,7 +211,7 @@ __global__ void __launch_bounds__(256, 4) spmv_panel_f32_kernel(Panels pan, cons
                                                              const int* __restrict__ kcell,
                                                              const int64_t* __restrict__ wOff,
                                                              const double* __restrict__ x, double* __restrict__ y,
-                                                             double* __restrict__ part, const PcgState* st) {
+                                                             double* __restrict__ part, PcgState* st) {
     if (st && st->done) return;
     constexpr int CH = 256;
     __shared__ __align__(16) float xh[2][CH];
@@ -284,6 +319,8 @@ __global__ void __launch_bounds__(256, 4) spmv_panel_f32_kernel(Panels pan, cons
             for (int i = 0; i < 8; ++i) s2 += red[i];
             part[blockIdx.x] = s2;
         }
+        // inside the PCG the last CTA also forms alpha
+        if (st && draw_last_ticket(st)) pcg_alpha_finish(part, gridDim.x, st);
     }
 }
 
@@ -325,6 +362,7 @@ __global__ void __launch_bounds__(256) pcg_init_scalars(const double* part, PcgS
     st->bb = bb;
     st->rr = bb;
     st->it = 0;
+    st->ticket = 0;
     st->status = ST_OK;
     st->done = bb == 0.0 ? 1 : 0;
 }
@@ -344,9 +382,13 @@ __global__ void __launch_bounds__(256) pcg_alpha_kernel(const double* part, int 
     st->alpha = st->rz / pq;
 }
 
-__global__ void pcg_update_xr_kernel(int64_t n, const PcgState* st, const double* __restrict__ p,
+// x += alpha p, r -= alpha q, z = P^{-1} r and the partials of r.r and r.z;
+// the last CTA then forms beta and the stopping test, and (fuse_p) also
+// p = z + beta p, which is cheaper than another launch for short vectors.
+__global__ void pcg_update_xr_kernel(int64_t n, PcgState* st, double* __restrict__ p,
                                      const double* __restrict__ q, const double* __restrict__ diag,
-                                     double* x, double* r, double* z, double* part) {
+                                     double* x, double* r, double* z, double* part, double tol2, int maxit,
+                                     int fuse_p) {
     if (st->done) return;
     const double alpha = st->alpha;
     double rr = 0.0, rz = 0.0;
@@ -365,31 +407,38 @@ __global__ void pcg_update_xr_kernel(int64_t n, const PcgState* st, const double
         part[blockIdx.x] = s1;
         part[kVecBlocks + blockIdx.x] = s2;
     }
-}
-
-__global__ void __launch_bounds__(256) pcg_beta_kernel(const double* part, PcgState* st, double tol2, int maxit) {
-    if (st->done) return;
+    if (!draw_last_ticket(st)) return;
     double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < kVecBlocks; i += blockDim.x) {
-        a += part[i];
-        b += part[kVecBlocks + i];
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        a += __ldcg(part + i);
+        b += __ldcg(part + kVecBlocks + i);
     }
-    const double rr = block_reduce(a);
-    const double rz = block_reduce(b);
-    if (threadIdx.x) return;
-    st->it += 1;
-    st->rr = rr;
-    st->beta = rz / st->rz;
-    st->rz = rz;
-    if (rr <= tol2 * st->bb) {
-        st->done = 1;
-    } else if (st->it >= maxit) {
-        st->status = ST_NOCONV;
-        st->done = 1;
+    const double rrs = block_reduce(a);
+    const double rzs = block_reduce(b);
+    __shared__ double beta_s;
+    __shared__ int go_on;
+    if (threadIdx.x == 0) {
+        st->it += 1;
+        st->rr = rrs;
+        st->beta = rzs / st->rz;
+        st->rz = rzs;
+        go_on = 0;
+        if (rrs <= tol2 * st->bb) {
+            st->done = 1;
+        } else if (st->it >= maxit) {
+            st->status = ST_NOCONV;
+            st->done = 1;
+        } else {
+            go_on = 1;
+        }
+        beta_s = st->beta;
     }
+    __syncthreads();
+    if (fuse_p && go_on)
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = __ldcg(z + i) + beta_s * p[i];
 }
 
-__global__ void pcg_update_p_kernel(int64_t n, const PcgState* st, const double* __restrict__ z, double* p) {
+__global__ void pcg_update_p_kernel(int64_t n, PcgState* st, const double* __restrict__ z, double* p) {
     if (st->done) return;
     const double beta = st->beta;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -426,7 +475,7 @@ __global__ void trend_solve_kernel(const double* part, int nb, int p, const doub
     for (int j = 0; j < p; ++j) beta[j] = y[j];
 }
 
-static void launch_spmv(mlb_ctx* ctx, const double* u, double* out, double* part, const PcgState* st) {
+static void launch_spmv(mlb_ctx* ctx, const double* u, double* out, double* part, PcgState* st) {
     if (ctx->pan.vals32) {
         if (ctx->pan.nwork == 0) {    // no wavelet rows: an empty product, a zero dot
             if (part) cudaMemsetAsync(part, 0, sizeof(double), ctx->stream);
@@ -441,7 +490,7 @@ static void launch_spmv(mlb_ctx* ctx, const double* u, double* out, double* part
 
 // y += eta x; part[block] = sum x_i y_i (when part != nullptr)
 __global__ void axpy_dot_kernel(int64_t n, double eta, const double* __restrict__ x, double* __restrict__ y,
-                                double* part, const PcgState* st) {
+                                double* part, PcgState* st) {
     if (st && st->done) return;
     double acc = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -455,7 +504,7 @@ __global__ void axpy_dot_kernel(int64_t n, double eta, const double* __restrict_
 
 // Three-step product of Sec. 6.2: out = W (K (W^T u)) + eta u, with the
 // kernel sum K a over all data points (no matrix is stored).
-static mlb_status three_step(mlb_ctx* ctx, const double* u, double* out, double* part, const PcgState* st) {
+static mlb_status three_step(mlb_ctx* ctx, const double* u, double* out, double* part, PcgState* st) {
     double* a = ctx->vec + 8 * ctx->N;
     double* b = ctx->vec + 9 * ctx->N;
     mlb_status s = apply_Wt_dev(ctx, u, a);
@@ -489,16 +538,24 @@ static mlb_status launch_iteration(mlb_ctx* ctx, double* x, double* r, double* z
         mlb_status s = three_step(ctx, p, q, ctx->partial, ctx->pcg);
         if (s != MLB_OK) return s;
         pcg_alpha_kernel<<<1, 256, 0, st>>>(ctx->partial, kVecBlocks, ctx->pcg);
+        ctx->launches += 1;
+    } else if (ctx->pan.vals32 && ctx->pan.nwork == 0) {
+        // no wavelet rows: nothing to iterate on
+        return MLB_OK;
     } else {
+        // the product's last CTA forms alpha
         launch_spmv(ctx, p, q, ctx->partial, ctx->pcg);
         ctx->launches += 1;
-        pcg_alpha_kernel<<<1, 256, 0, st>>>(ctx->partial, ctx->pan.vals32 ? std::max(ctx->pan.nwork, 1) : ctx->ncell,
-                                           ctx->pcg);
     }
-    pcg_update_xr_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, p, q, diag, x, r, z, part2);
-    pcg_beta_kernel<<<1, 256, 0, st>>>(part2, ctx->pcg, tol2, ctx->opts.pcg_maxit);
-    pcg_update_p_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, z, p);
-    ctx->launches += 4;
+    // short vectors: the last CTA of the update also forms p; long ones get a launch
+    const int fuse_p = n <= kFusePMax ? 1 : 0;
+    pcg_update_xr_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, p, q, diag, x, r, z, part2, tol2,
+                                                     ctx->opts.pcg_maxit, fuse_p);
+    ctx->launches += 1;
+    if (!fuse_p) {
+        pcg_update_p_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, z, p);
+        ctx->launches += 1;
+    }
     return MLB_OK;
 }
 
@@ -517,44 +574,48 @@ mlb_status pcg_run(mlb_ctx* ctx, const double* b, double* x, mlb_info* info) {
     MLB_CHECK_LAUNCH(ctx, "pcg_init");
     ctx->launches += 1;
     const double tol2 = ctx->opts.pcg_rtol * ctx->opts.pcg_rtol;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, st);
+    // graph, its instance and the timing events are released on every return
+    struct Owned {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        ~Owned() {
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+    } own;
+    MLB_CUDA(ctx, cudaEventCreate(&own.e0));
+    MLB_CUDA(ctx, cudaEventCreate(&own.e1));
+    MLB_CUDA(ctx, cudaEventRecord(own.e0, st));
     // one chunk of iterations as a CUDA graph, replayed until done
     const int chunk = ctx->opts.matrix_free ? 2 : 8;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
     const int64_t l0 = ctx->launches;
     MLB_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < chunk; ++i) {
         mlb_status ls = launch_iteration(ctx, x, r, z, p, q, tol2);
         if (ls != MLB_OK) {
-            cudaStreamEndCapture(st, &graph);
-            if (graph) cudaGraphDestroy(graph);
+            cudaStreamEndCapture(st, &own.graph);
             return ls;
         }
     }
-    MLB_CUDA(ctx, cudaStreamEndCapture(st, &graph));
-    MLB_CUDA(ctx, cudaGraphInstantiate(&exec, graph, 0));
+    MLB_CUDA(ctx, cudaStreamEndCapture(st, &own.graph));
+    MLB_CUDA(ctx, cudaGraphInstantiate(&own.exec, own.graph, 0));
     const int64_t perChunk = ctx->launches - l0;   // kernels in one replay (capture counted them once)
     ctx->launches = l0;
     PcgState hs{};
     for (;;) {
-        MLB_CUDA(ctx, cudaGraphLaunch(exec, st));
+        MLB_CUDA(ctx, cudaGraphLaunch(own.exec, st));
         ctx->launches += perChunk;
         MLB_CUDA(ctx, cudaMemcpyAsync(&hs, ctx->pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, st));
         MLB_CUDA(ctx, cudaStreamSynchronize(st));
         if (hs.done) break;
     }
-    cudaEventRecord(e1, st);
-    cudaEventSynchronize(e1);
+    MLB_CUDA(ctx, cudaEventRecord(own.e1, st));
+    MLB_CUDA(ctx, cudaEventSynchronize(own.e1));
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
+    cudaEventElapsedTime(&ms, own.e0, own.e1);
     if (info) {
         info->iterations = hs.it;
         info->converged = hs.status == ST_OK && hs.done;
