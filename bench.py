@@ -406,7 +406,7 @@ def run_ours(args, rank, world, local_rank):
     else:
         # FP64 panels: one FMA per entry; GB300's FP64 rate (nominal 1.25 TFLOP/s)
         # is below what 8 bytes per entry at HBM speed would need
-        kname = "spmv_panel_kernel<double>"
+        kname = "spmv_panel_f64_kernel"
         flops = 2.0 * info["nnz"]
         achieved = flops / (head["spmv_ms"] / 1000.0) / 1e12
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,

@@ -77,31 +77,16 @@ __device__ void pcg_alpha_finish(const double* part, int nparts, PcgState* st) {
 // keep enough bytes in flight every lane issues the loads of four rows times
 // four 16-byte segments before it consumes any of them (panels are padded to
 // a width that is a multiple of 4, so every row starts 16-byte aligned).
-// FP64 panels multiply in FP64 (on GB300 the FP64 pipe, not HBM, bounds this
-// product); FP32 panels multiply FP32 values by the FP32-rounded x.
+// FP64 throughout: on GB300 the FP64 pipe, not HBM, bounds this product.
 // Optionally part[block] = sum over the panel's rows of x_r y_r.
-template <typename T>
-struct Vec2;
-template <>
-struct Vec2<double> {
-    using type = double2;
-};
-template <>
-struct Vec2<float> {
-    using type = float2;
-};
-
-template <typename T>
-__global__ void __launch_bounds__(256) spmv_panel_kernel(Panels pan, const T* __restrict__ vals,
-                                                         const int* __restrict__ kcell,
-                                                         const int64_t* __restrict__ wOff, int ncell,
-                                                         const double* __restrict__ x, double* __restrict__ y,
-                                                         double* __restrict__ part, PcgState* st) {
+__global__ void __launch_bounds__(256) spmv_panel_f64_kernel(Panels pan, const double* __restrict__ vals,
+                                                             const int* __restrict__ kcell,
+                                                             const int64_t* __restrict__ wOff, int ncell,
+                                                             const double* __restrict__ x, double* __restrict__ y,
+                                                             double* __restrict__ part, PcgState* st) {
     if (st && st->done) return;
-    using V2 = typename Vec2<T>::type;
     constexpr int CH = 256;
-    __shared__ T xs[CH];          // the chunk's x values, in the panel's arithmetic type
-    __shared__ T xl[CH];          // FP32 panels: the low part of x (x = x_hi + x_lo)
+    __shared__ double xs[CH];     // the chunk's x values
     __shared__ double red[8];
     const int g = ncell - 1 - blockIdx.x;
     const int kc = kcell[g];
@@ -110,49 +95,42 @@ __global__ void __launch_bounds__(256) spmv_panel_kernel(Panels pan, const T* __
     if (kc > 0) {
         const int n = pan.ncols[g];
         const int* ci = pan.colidx + pan.colOff[g];
-        const T* v0 = vals + pan.valOff[g];
+        const double* v0 = vals + pan.valOff[g];
         const int64_t r0 = wOff[g];
         const int nrg = (kc + 31) / 32;          // groups of 4 rows per warp actually used
-        // FP64: plain sums.  FP32: one chunk's 8 products per lane in FP32, the
-        // running sum over chunks a cascaded FP32 sum (no FP64 in the loop).
-        T acc[8], cmp[8];
+        // one DFMA per entry (the FP64 pipe bounds this kernel on GB300): each
+        // lane chains its 8 products of a chunk, one add per chunk into the row
+        double acc[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = cmp[q] = (T)0;
+        for (int q = 0; q < 8; ++q) acc[q] = 0.0;
         for (int c0 = 0; c0 < n; c0 += CH) {
             const int m = min(CH, n - c0);
             __syncthreads();
-            if (threadIdx.x < m) {
-                const double xv = x[ci[c0 + threadIdx.x]];
-                xs[threadIdx.x] = (T)xv;
-                if constexpr (sizeof(T) == 4) xl[threadIdx.x] = (T)(xv - (double)(T)xv);
-            }
+            if (threadIdx.x < m) xs[threadIdx.x] = x[ci[c0 + threadIdx.x]];
             __syncthreads();
             if (m == CH) {
 #pragma unroll
                 for (int qb = 0; qb < 2; ++qb) {
                     if (qb >= nrg) break;
-                    V2 v[4][4];
+                    double2 v[4][4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int r = warp + 8 * (4 * qb + q);
-                        const T* row = v0 + (int64_t)min(r, kc - 1) * n + c0 + 2 * lane;
+                        const double* row = v0 + (int64_t)min(r, kc - 1) * n + c0 + 2 * lane;
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) v[q][u] = *reinterpret_cast<const V2*>(row + 64 * u);
+                        for (int u = 0; u < 4; ++u) v[q][u] = *reinterpret_cast<const double2*>(row + 64 * u);
                     }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int r = warp + 8 * (4 * qb + q);
-                        T a = (T)0;
+                        double a = 0.0;
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const int j = 2 * lane + 64 * u;
-                            a += v[q][u].x * xs[j] + v[q][u].y * xs[j + 1];
-                            if constexpr (sizeof(T) == 4) a += v[q][u].x * xl[j] + v[q][u].y * xl[j + 1];
+                            a = fma(v[q][u].x, xs[j], a);
+                            a = fma(v[q][u].y, xs[j + 1], a);
                         }
-                        if (r < kc) {
-                            if constexpr (sizeof(T) == 4) sum2_add(acc[4 * qb + q], cmp[4 * qb + q], a);
-                            else acc[4 * qb + q] += a;
-                        }
+                        if (r < kc) acc[4 * qb + q] += a;
                     }
                 }
             } else {
@@ -160,15 +138,14 @@ __global__ void __launch_bounds__(256) spmv_panel_kernel(Panels pan, const T* __
                 for (int q = 0; q < 8; ++q) {
                     const int r = warp + 8 * q;
                     if (r < kc) {
-                        const T* row = v0 + (int64_t)r * n + c0;
-                        T a = (T)0;
+                        const double* row = v0 + (int64_t)r * n + c0;
+                        double a = 0.0;
                         for (int j = 2 * lane; j < m; j += 64) {
-                            const V2 vv = *reinterpret_cast<const V2*>(row + j);
-                            a += vv.x * xs[j] + vv.y * xs[j + 1];
-                            if constexpr (sizeof(T) == 4) a += vv.x * xl[j] + vv.y * xl[j + 1];
+                            const double2 vv = *reinterpret_cast<const double2*>(row + j);
+                            a = fma(vv.x, xs[j], a);
+                            a = fma(vv.y, xs[j + 1], a);
                         }
-                        if constexpr (sizeof(T) == 4) sum2_add(acc[q], cmp[q], a);
-                        else acc[q] += a;
+                        acc[q] += a;
                     }
                 }
             }
@@ -176,7 +153,7 @@ __global__ void __launch_bounds__(256) spmv_panel_kernel(Panels pan, const T* __
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int r = warp + 8 * q;
-            double a = (double)acc[q] + (double)cmp[q];
+            double a = acc[q];
             for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
             if (lane == 0 && r < kc) {
                 y[r0 + r] = a;
@@ -484,7 +461,7 @@ static void launch_spmv(mlb_ctx* ctx, const double* u, double* out, double* part
         spmv_panel_f32_kernel<<<ctx->pan.nwork, 256, 0, ctx->stream>>>(ctx->pan, ctx->pan.vals32, ctx->cells.k,
                                                                       ctx->cells.wOff, u, out, part, st);
     } else
-        spmv_panel_kernel<double><<<ctx->ncell, 256, 0, ctx->stream>>>(ctx->pan, ctx->pan.vals, ctx->cells.k,
+        spmv_panel_f64_kernel<<<ctx->ncell, 256, 0, ctx->stream>>>(ctx->pan, ctx->pan.vals, ctx->cells.k,
                                                                       ctx->cells.wOff, ctx->ncell, u, out, part, st);
 }
 
@@ -522,7 +499,7 @@ static mlb_status three_step(mlb_ctx* ctx, const double* u, double* out, double*
 mlb_status cw_matvec_dev(mlb_ctx* ctx, const double* u, double* out) {
     if (ctx->opts.matrix_free) return three_step(ctx, u, out, nullptr, nullptr);
     launch_spmv(ctx, u, out, nullptr, nullptr);
-    MLB_CHECK_LAUNCH(ctx, "spmv_panel_kernel");
+    MLB_CHECK_LAUNCH(ctx, "spmv_panel kernel");
     return MLB_OK;
 }
 
