@@ -758,8 +758,8 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
         // product runs one CTA per 32 rows of a panel, heaviest items first.
         std::vector<std::pair<int64_t, int2>> items;
         for (int g = 0; g < ncell; ++g)
-            for (int r = 0; r < ctx->hcells[g].k; r += 32)
-                items.push_back({-(int64_t)std::min(32, ctx->hcells[g].k - r) * padded[g], make_int2(g, r)});
+            for (int r = 0; r < ctx->hcells[g].k; r += kItemRows)
+                items.push_back({-(int64_t)std::min(kItemRows, ctx->hcells[g].k - r) * padded[g], make_int2(g, r)});
         std::stable_sort(items.begin(), items.end(),
                          [](const std::pair<int64_t, int2>& x, const std::pair<int64_t, int2>& y) {
                              return x.first < y.first;

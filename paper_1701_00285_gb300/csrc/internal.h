@@ -57,9 +57,13 @@ struct Panels {
     int nwork = 0;
 };
 
-// Upper bound on the FP32 product's work items (at most 32 rows each): the
-// cells hold nwav <= N rows, so sum over cells of ceil(k / 32) <= ncell + N / 32.
-inline size_t max_work_items(int ncell, int64_t N) { return (size_t)ncell + (size_t)(N / 32) + 1; }
+// Rows of one work item of the FP32 product (one CTA of 8 warps, up to 4 rows
+// per warp).
+constexpr int kItemRows = 32;
+
+// Upper bound on the FP32 product's work items: the cells hold nwav <= N
+// rows, so the sum over cells of ceil(k / kItemRows) <= ncell + N / kItemRows.
+inline size_t max_work_items(int ncell, int64_t N) { return (size_t)ncell + (size_t)(N / kItemRows) + 1; }
 
 struct PcgState {
     double rz, rr, bb, alpha, beta, pq;

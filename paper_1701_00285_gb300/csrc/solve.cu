@@ -174,10 +174,11 @@ __global__ void __launch_bounds__(256) spmv_panel_f64_kernel(Panels pan, const d
     }
 }
 
-// FP32 panels: one CTA per work item of at most 32 rows of a panel (the
+// FP32 panels: one CTA per work item of at most kItemRows rows of a panel (the
 // heaviest items first, so that the uneven panels fill the SMs evenly); each
-// warp owns four rows and loads, per 256-column chunk, two 16-byte vectors of
-// each of them before using any (128 bytes per lane in flight).  x is staged
+// warp owns kItemRows / 8 rows and loads, per 256-column chunk, two 16-byte
+// vectors of each of them before using any (128 bytes per lane in flight at
+// 32-row items).  x is staged
 // per chunk as FP32 high and low parts in a double buffer: the gather of the
 // next chunk's x (column list -> x, an L2 round trip) is issued before the
 // current chunk is multiplied and stored after it, so one barrier per chunk
@@ -196,17 +197,18 @@ __global__ void __launch_bounds__(256, 4) spmv_panel_f32_kernel(Panels pan, cons
     __shared__ double red[8];
     const int2 wk = pan.work[blockIdx.x];
     const int g = wk.x;
-    const int rows = min(32, kcell[g] - wk.y);
+    const int rows = min(kItemRows, kcell[g] - wk.y);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = pan.ncols[g];
     const int* ci = pan.colidx + pan.colOff[g];
     const int64_t nn = n;
     const float* v0 = vals + pan.valOff[g] + (int64_t)wk.y * nn;
     const int64_t r0 = wOff[g] + wk.y;
-    const int nq = min(4, (rows - warp + 7) / 8);      // rows of this warp: warp, warp + 8, ...
-    float acc[4], err[4];
+    constexpr int QR = kItemRows / 8;                  // rows per warp
+    const int nq = min(QR, (rows - warp + 7) / 8);     // rows of this warp: warp, warp + 8, ...
+    float acc[QR], err[QR];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = err[q] = 0.0f;
+    for (int q = 0; q < QR; ++q) acc[q] = err[q] = 0.0f;
     if (threadIdx.x < min(CH, n)) {
         const double xv = x[ci[threadIdx.x]];
         const float h = (float)xv;
@@ -231,16 +233,16 @@ __global__ void __launch_bounds__(256, 4) spmv_panel_f32_kernel(Panels pan, cons
         const float* sh = xh[buf];
         const float* sl = xl[buf];
         if (m == CH) {
-            float4 v[4][2];
+            float4 v[QR][2];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < QR; ++q) {
                 const int r = min(warp + 8 * q, rows - 1);
                 const float* row = v0 + (int64_t)r * nn + c0 + 4 * lane;
 #pragma unroll
                 for (int u = 0; u < 2; ++u) v[q][u] = *reinterpret_cast<const float4*>(row + 128 * u);
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < QR; ++q) {
                 if (q < nq) {
                     float a = 0.0f;
 #pragma unroll
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(256, 4) spmv_panel_f32_kernel(Panels pan, cons
             }
         } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < QR; ++q) {
                 if (q < nq) {
                     const float* row = v0 + (int64_t)(warp + 8 * q) * nn + c0;
                     float a = 0.0f;
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(256, 4) spmv_panel_f32_kernel(Panels pan, cons
     }
     double dotp = 0.0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < QR; ++q) {
         double a = (double)acc[q] + (double)err[q];
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
         const int r = warp + 8 * q;
