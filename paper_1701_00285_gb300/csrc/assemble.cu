@@ -755,21 +755,38 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
     dfree(A, X1);
     if (mixed) {
         // the mixed path keeps C~_W in FP32: half the bytes per product.  Its
-        // product runs one CTA per 32 rows of a panel, heaviest items first.
-        std::vector<std::pair<int64_t, int2>> items;
-        for (int g = 0; g < ncell; ++g)
+        // product runs one CTA per kItemRows rows x kSegCols columns of a
+        // panel, heaviest items first, so the last wave of CTAs is short.
+        std::vector<std::pair<int64_t, int4>> items;
+        std::vector<int> nseg(ncell, 0);
+        int nsegMax = 1;
+        for (int g = 0; g < ncell; ++g) {
+            if (ctx->hcells[g].k == 0) continue;
+            nseg[g] = (padded[g] + kSegCols - 1) / kSegCols;
+            nsegMax = std::max(nsegMax, nseg[g]);
             for (int r = 0; r < ctx->hcells[g].k; r += kItemRows)
-                items.push_back({-(int64_t)std::min(kItemRows, ctx->hcells[g].k - r) * padded[g], make_int2(g, r)});
+                for (int sg = 0; sg < nseg[g]; ++sg) {
+                    const int cb = sg * kSegCols;
+                    const int64_t w = (int64_t)std::min(kItemRows, ctx->hcells[g].k - r) *
+                                      std::min(kSegCols, padded[g] - cb);
+                    items.push_back({-w, make_int4(g, r, cb, sg)});
+                }
+        }
         std::stable_sort(items.begin(), items.end(),
-                         [](const std::pair<int64_t, int2>& x, const std::pair<int64_t, int2>& y) {
+                         [](const std::pair<int64_t, int4>& x, const std::pair<int64_t, int4>& y) {
                              return x.first < y.first;
                          });
-        std::vector<int2> work;
+        std::vector<int4> work;
         for (auto& it : items) work.push_back(it.second);
+        if (work.size() > max_work_items(ncell, ctx->N)) return fail(ctx, MLB_EINVAL, "work table bound");
         pan.nwork = (int)work.size();
-        pan.work = (int2*)dalloc(ctx, A, sizeof(int2) * std::max<size_t>(1, work.size()));
-        if (!pan.work) return MLB_ENOMEM;
-        MLB_CUDA(ctx, cudaMemcpyAsync(pan.work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, st));
+        pan.nsegMax = nsegMax;
+        pan.work = (int4*)dalloc(ctx, A, sizeof(int4) * std::max<size_t>(1, work.size()));
+        pan.nseg = (int*)dalloc(ctx, A, sizeof(int) * ncell);
+        pan.ypart = (double*)dalloc(ctx, A, sizeof(double) * std::max<int64_t>(1, (int64_t)nsegMax * ctx->nwav));
+        if (!pan.work || !pan.nseg || !pan.ypart) return MLB_ENOMEM;
+        MLB_CUDA(ctx, cudaMemcpyAsync(pan.work, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice, st));
+        MLB_CUDA(ctx, cudaMemcpyAsync(pan.nseg, nseg.data(), sizeof(int) * ncell, cudaMemcpyHostToDevice, st));
         MLB_CUDA(ctx, cudaStreamSynchronize(st));
         pan.vals32 = (float*)dalloc(ctx, A, sizeof(float) * std::max<int64_t>(1, stored));
         if (!pan.vals32) return MLB_ENOMEM;

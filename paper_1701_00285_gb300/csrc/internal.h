@@ -53,17 +53,27 @@ struct Panels {
     int* rowCell = nullptr;     // per wavelet row: its cell
     double* vals = nullptr;     // FP64 values
     float* vals32 = nullptr;    // FP32 copy (mixed precision)
-    int2* work = nullptr;       // FP32 product: (cell, first row) of each CTA, heaviest first
+    // FP32 product: one CTA per (cell, first row, first column, segment) of at
+    // most kItemRows rows and kSegCols columns, heaviest first; the segments'
+    // partial rows go to ypart (segment-major) and are summed in order
+    int4* work = nullptr;
     int nwork = 0;
+    int* nseg = nullptr;        // per cell: column segments of its panel
+    double* ypart = nullptr;    // nsegMax x nwav partial products
+    int nsegMax = 0;
 };
 
-// Rows of one work item of the FP32 product (one CTA of 8 warps, up to 4 rows
-// per warp).
+// Rows and columns of one work item of the FP32 product (one CTA of 8 warps,
+// up to 4 rows per warp; the column range a multiple of the 256-column chunk).
 constexpr int kItemRows = 32;
+constexpr int kSegCols = 8192;
 
-// Upper bound on the FP32 product's work items: the cells hold nwav <= N
-// rows, so the sum over cells of ceil(k / kItemRows) <= ncell + N / kItemRows.
-inline size_t max_work_items(int ncell, int64_t N) { return (size_t)ncell + (size_t)(N / kItemRows) + 1; }
+// Upper bound on the FP32 product's work items: the cells hold nwav <= N rows
+// and at most N columns, so the count is at most
+// (ncell + N / kItemRows) x ceil(N / kSegCols).
+inline size_t max_work_items(int ncell, int64_t N) {
+    return ((size_t)ncell + (size_t)(N / kItemRows) + 1) * (size_t)((N + kSegCols - 1) / kSegCols);
+}
 
 struct PcgState {
     double rz, rr, bb, alpha, beta, pq;

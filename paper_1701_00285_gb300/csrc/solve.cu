@@ -174,8 +174,10 @@ __global__ void __launch_bounds__(256) spmv_panel_f64_kernel(Panels pan, const d
     }
 }
 
-// FP32 panels: one CTA per work item of at most kItemRows rows of a panel (the
-// heaviest items first, so that the uneven panels fill the SMs evenly); each
+// FP32 panels: one CTA per work item of at most kItemRows rows and kSegCols
+// columns of a panel (the heaviest items first, so that the uneven panels fill
+// the SMs evenly and the last wave is short); the item writes its rows'
+// partial products to its column segment's slice of ypart.  Each
 // warp owns kItemRows / 8 rows and loads, per 256-column chunk, two 16-byte
 // vectors of each of them before using any (128 bytes per lane in flight at
 // 32-row items).  x is staged
@@ -188,20 +190,22 @@ __global__ void __launch_bounds__(256) spmv_panel_f64_kernel(Panels pan, const d
 __global__ void __launch_bounds__(256, 4) spmv_panel_f32_kernel(Panels pan, const float* __restrict__ vals,
                                                              const int* __restrict__ kcell,
                                                              const int64_t* __restrict__ wOff,
-                                                             const double* __restrict__ x, double* __restrict__ y,
+                                                             const double* __restrict__ x, int64_t nwav,
                                                              double* __restrict__ part, PcgState* st) {
     if (st && st->done) return;
     constexpr int CH = 256;
     __shared__ __align__(16) float xh[2][CH];
     __shared__ __align__(16) float xl[2][CH];
     __shared__ double red[8];
-    const int2 wk = pan.work[blockIdx.x];
+    const int4 wk = pan.work[blockIdx.x];           // cell, first row, first column, segment
     const int g = wk.x;
     const int rows = min(kItemRows, kcell[g] - wk.y);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int n = pan.ncols[g];
+    const int64_t nn = pan.ncols[g];                  // row stride of the panel
+    const int cb = wk.z;
+    const int n = min((int)nn, cb + kSegCols);        // end of this item's columns
     const int* ci = pan.colidx + pan.colOff[g];
-    const int64_t nn = n;
+    double* __restrict__ y = pan.ypart + (int64_t)wk.w * nwav;
     const float* v0 = vals + pan.valOff[g] + (int64_t)wk.y * nn;
     const int64_t r0 = wOff[g] + wk.y;
     constexpr int QR = kItemRows / 8;                  // rows per warp
@@ -209,15 +213,15 @@ __global__ void __launch_bounds__(256, 4) spmv_panel_f32_kernel(Panels pan, cons
     float acc[QR], err[QR];
 #pragma unroll
     for (int q = 0; q < QR; ++q) acc[q] = err[q] = 0.0f;
-    if (threadIdx.x < min(CH, n)) {
-        const double xv = x[ci[threadIdx.x]];
+    if (threadIdx.x < min(CH, n - cb)) {
+        const double xv = x[ci[cb + threadIdx.x]];
         const float h = (float)xv;
         xh[0][threadIdx.x] = h;
         xl[0][threadIdx.x] = (float)(xv - (double)h);
     }
     __syncthreads();
     int buf = 0;
-    for (int c0 = 0; c0 < n; c0 += CH) {
+    for (int c0 = cb; c0 < n; c0 += CH) {
         const int m = min(CH, n - c0);
         const int cn = c0 + CH + threadIdx.x;
         // one thread per row asks the L2 for the row's next chunk (a bulk
@@ -364,16 +368,28 @@ __global__ void __launch_bounds__(256) pcg_alpha_kernel(const double* part, int 
 // x += alpha p, r -= alpha q, z = P^{-1} r and the partials of r.r and r.z;
 // the last CTA then forms beta and the stopping test, and (fuse_p) also
 // p = z + beta p, which is cheaper than another launch for short vectors.
+// With ypart != nullptr, q_i is the in-order sum of the FP32 product's
+// segment partials (nseg[rowCell[i]] of them).
 __global__ void pcg_update_xr_kernel(int64_t n, PcgState* st, double* __restrict__ p,
-                                     const double* __restrict__ q, const double* __restrict__ diag,
+                                     const double* __restrict__ q, const double* __restrict__ ypart,
+                                     const int* __restrict__ rowCell, const int* __restrict__ nseg,
+                                     const double* __restrict__ diag,
                                      double* x, double* r, double* z, double* part, double tol2, int maxit,
                                      int fuse_p) {
     if (st->done) return;
     const double alpha = st->alpha;
     double rr = 0.0, rz = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double qi;
+        if (ypart) {
+            const int ns = nseg[rowCell[i]];
+            qi = 0.0;
+            for (int sg = 0; sg < ns; ++sg) qi += ypart[sg * n + i];
+        } else {
+            qi = q[i];
+        }
         x[i] += alpha * p[i];
-        const double ri = r[i] - alpha * q[i];
+        const double ri = r[i] - alpha * qi;
         r[i] = ri;
         const double zi = diag ? ri / diag[i] : ri;
         z[i] = zi;
@@ -454,14 +470,34 @@ __global__ void trend_solve_kernel(const double* part, int nb, int p, const doub
     for (int j = 0; j < p; ++j) beta[j] = y[j];
 }
 
-static void launch_spmv(mlb_ctx* ctx, const double* u, double* out, double* part, PcgState* st) {
+// y_i = sum over the column segments of row i's panel of ypart[s][i], in order
+__global__ void seg_reduce_kernel(int64_t n, const int* __restrict__ rowCell, const int* __restrict__ nseg,
+                                  const double* __restrict__ ypart, double* __restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int ns = nseg[rowCell[i]];
+        double v = 0.0;
+        for (int sg = 0; sg < ns; ++sg) v += ypart[sg * n + i];
+        y[i] = v;
+    }
+}
+
+// out = C~_W u.  The FP32 product leaves its segment partials in ypart; inside
+// the PCG (sum_in_update) the vector update sums them, elsewhere a reduction
+// writes out.
+static void launch_spmv(mlb_ctx* ctx, const double* u, double* out, double* part, PcgState* st,
+                        bool sum_in_update = false) {
     if (ctx->pan.vals32) {
         if (ctx->pan.nwork == 0) {    // no wavelet rows: an empty product, a zero dot
             if (part) cudaMemsetAsync(part, 0, sizeof(double), ctx->stream);
             return;
         }
         spmv_panel_f32_kernel<<<ctx->pan.nwork, 256, 0, ctx->stream>>>(ctx->pan, ctx->pan.vals32, ctx->cells.k,
-                                                                      ctx->cells.wOff, u, out, part, st);
+                                                                      ctx->cells.wOff, u, ctx->nwav, part, st);
+        if (!sum_in_update) {
+            seg_reduce_kernel<<<kVecBlocks, 256, 0, ctx->stream>>>(ctx->nwav, ctx->pan.rowCell, ctx->pan.nseg,
+                                                                   ctx->pan.ypart, out);
+            ctx->launches += 1;
+        }
     } else
         spmv_panel_f64_kernel<<<ctx->ncell, 256, 0, ctx->stream>>>(ctx->pan, ctx->pan.vals, ctx->cells.k,
                                                                       ctx->cells.wOff, ctx->ncell, u, out, part, st);
@@ -522,13 +558,16 @@ static mlb_status launch_iteration(mlb_ctx* ctx, double* x, double* r, double* z
         // no wavelet rows: nothing to iterate on
         return MLB_OK;
     } else {
-        // the product's last CTA forms alpha
-        launch_spmv(ctx, p, q, ctx->partial, ctx->pcg);
+        // the product's last CTA forms alpha; the FP32 product's segment
+        // partials are summed by the update below
+        launch_spmv(ctx, p, q, ctx->partial, ctx->pcg, true);
         ctx->launches += 1;
     }
+    const bool segs = !ctx->opts.matrix_free && ctx->pan.vals32;
     // short vectors: the last CTA of the update also forms p; long ones get a launch
     const int fuse_p = n <= kFusePMax ? 1 : 0;
-    pcg_update_xr_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, p, q, diag, x, r, z, part2, tol2,
+    pcg_update_xr_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, p, q, segs ? ctx->pan.ypart : nullptr,
+                                                     ctx->pan.rowCell, ctx->pan.nseg, diag, x, r, z, part2, tol2,
                                                      ctx->opts.pcg_maxit, fuse_p);
     ctx->launches += 1;
     if (!fuse_p) {
