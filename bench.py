@@ -340,29 +340,59 @@ def e2e_run(ctx, P, args, world, torch):
             "d2h_bytes_per_step": int(hy.nbytes + hb.nbytes)}
 
 
+def shard_indices(count: int, rank: int, world: int) -> range:
+    """Problems of one rank: its own slice of the world x count problems the
+    generator draws (weak scaling; ranks share nothing)."""
+    return range(rank * count, (rank + 1) * count)
+
+
+def barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_batched(args, rank, world, local_rank):
-    """Batched workload: every step solves all problems in one mlb_batch_solve."""
+    """Batched workload: every step solves this rank's problems in one
+    mlb_batch_solve (host buffers in, predictions out: end to end)."""
     import torch
     import workloads as wl
-    from paper_1701_00285_gb300.binding import batch_solve
+    from paper_1701_00285_gb300.binding import batch_last_launches, batch_last_phase_ms, batch_solve
     torch.cuda.set_device(local_rank)
-    probs = wl.config4(count=args.count)
+    dev = torch.device("cuda", local_rank)
+    every = wl.config4(count=args.count * world)
+    probs = [every[i] for i in shard_indices(args.count, rank, world)]
     items = [{"points": q.points, "w": q.w, "nu": q.nu, "rho": q.rho, "nugget": q.nugget,
               "tau_factor": q.tau_factor, "Z": q.Z, "targets": q.targets} for q in probs]
+    h2d = sum(q.points.nbytes + q.Z.nbytes + q.targets.nbytes for q in probs)
+    d2h = sum(q.targets.shape[0] * 8 + math.comb(q.d + q.w, q.w) * 8 for q in probs)
     out = {}
     for prec in ("mixed", "fp64"):
         for _ in range(args.warmup):
             res, ms, st = batch_solve(items, precision=prec, pcg_rtol=1e-10, pcg_maxit=50000, device=local_rank)
-        times = []
+        launches = 0
         with ClockSampler(local_rank) as clk:
+            barrier(world)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             for _ in range(args.steps):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
                 res, ms, st = batch_solve(items, precision=prec, pcg_rtol=1e-10, pcg_maxit=50000, device=local_rank)
-                torch.cuda.synchronize()
-                times.append(time.perf_counter() - t0)
-        out[prec] = {"res": res, "s": sum(times), "status": st, "clocks": clk.summary(),
-                     "its": [r[3] for r in res]}
+                launches += batch_last_launches()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            barrier(world)
+        out[prec] = {"res": res, "s": max_over_ranks(dt, world, dev), "status": st, "clocks": clk.summary(),
+                     "its": [r[3] for r in res], "phases": batch_last_phase_ms(), "launches": launches}
     ym = np.concatenate([r[0] for r in out["mixed"]["res"]])
     yd = np.concatenate([r[0] for r in out["fp64"]["res"]])
     per = [float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0])) for a, b in zip(out["mixed"]["res"], out["fp64"]["res"])]
@@ -370,13 +400,17 @@ def run_batched(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": "BLUP solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * out["mixed"]["s"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-            "config": {"workload": f"config4: {args.count} independent problems, n log-uniform [500, 8000], "
+            "config": {"workload": f"config4: {args.count} independent problems per GPU, n log-uniform [500, 8000], "
                                    f"d in {{2,3,5}}, nu in {{1/2,3/2,5/2}}, rho ~ U[0.1,0.5], w=1, leaf 64, "
-                                   f"tau=2 diameters, nugget 1e-4, PCG tol 1e-10, 1024 targets each",
-                       "precision": "mixed", "parallelism": f"replicas{world}",
+                                   f"tau=inf, nugget 1e-4, PCG tol 1e-10, 1024 targets each",
+                       "precision": "mixed", "parallelism": f"problem-sharded{world}",
                        "cache": "inputs copied from the host each step (batched API takes host buffers)"},
+            "e2e": {"value": value, "unit": "BLUP solves/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": out["mixed"]["launches"],
+            "phases_ms": out["mixed"]["phases"],
             "fp64": {"value": world * args.count * args.steps / out["fp64"]["s"],
-                     "ms_per_step": 1000 * out["fp64"]["s"] / args.steps},
+                     "ms_per_step": 1000 * out["fp64"]["s"] / args.steps, "phases_ms": out["fp64"]["phases"]},
             "mixed_vs_fp64": {"rel_pred_err_max": max(per), "rel_pred_err_all": float(np.linalg.norm(ym - yd) / np.linalg.norm(yd)),
                               "speedup": out["fp64"]["s"] / out["mixed"]["s"]},
             "pcg_iterations": {"median": float(np.median(out["mixed"]["its"])), "max": int(max(out["mixed"]["its"]))},

@@ -185,6 +185,9 @@ const char* mlb_batch_last_error(void);
  * by phase: [0] setup (basis, assembly, Z_W), [1] PCG, [2] closing (gamma,
  * trend, predictions, context release).  out: 3 doubles (host). */
 void mlb_batch_last_phase_ms(double* out);
+/* Kernels launched by the last mlb_batch_solve on the calling thread (all
+ * problems' kernels plus the one persistent PCG launch). */
+int64_t mlb_batch_last_launches(void);
 
 /* ---- inspection (tests and tools) ---------------------------------------- */
 

@@ -77,6 +77,7 @@ _SIGS = {
                                        ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "mlb_batch_last_error": (ctypes.c_char_p, []),
     "mlb_batch_last_phase_ms": (None, [ctypes.POINTER(ctypes.c_double)]),
+    "mlb_batch_last_launches": (ctypes.c_int64, []),
     "mlb_get_sizes": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(_I64)]),
@@ -156,6 +157,11 @@ def batch_solve(problems, precision: str = "fp64", leaf_size: int = 64, pcg_rtol
         import warnings
         warnings.warn("mlb_batch_solve: " + L.mlb_batch_last_error().decode())
     return res, ms.value, st
+
+
+def batch_last_launches() -> int:
+    """Kernels launched by the calling thread's last batch_solve."""
+    return int(lib().mlb_batch_last_launches())
 
 
 def batch_last_phase_ms() -> dict:

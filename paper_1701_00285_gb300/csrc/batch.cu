@@ -191,6 +191,7 @@ namespace {
 
 thread_local std::string g_batch_err;
 thread_local double g_batch_phase_ms[3] = {0.0, 0.0, 0.0};
+thread_local int64_t g_batch_launches = 0;
 
 double ms_since(std::chrono::steady_clock::time_point t) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
@@ -274,6 +275,8 @@ void run_parallel(std::vector<Job>& jobs, int threads, F f) {
 
 extern "C" const char* mlb_batch_last_error(void) { return g_batch_err.c_str(); }
 
+extern "C" int64_t mlb_batch_last_launches(void) { return g_batch_launches; }
+
 extern "C" void mlb_batch_last_phase_ms(double* out) {
     if (out)
         for (int i = 0; i < 3; ++i) out[i] = g_batch_phase_ms[i];
@@ -301,6 +304,7 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
     }
     // phase 1: basis, assembly, Z_W
     for (double& v : g_batch_phase_ms) v = 0.0;
+    g_batch_launches = 0;
     auto tp = std::chrono::steady_clock::now();
     run_parallel(jobs, threads, [&](Job& j, int t) {
         cudaSetDevice(o.device);
@@ -316,7 +320,6 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
         if (jobs[i].status == MLB_OK) (jobs[i].ctx->nwav > kCtaRows ? big : order).push_back(i);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].ctx->nwav > jobs[b].ctx->nwav; });
     std::vector<BatchPcgProblem> hp;
-    std::vector<int> idx;
     for (int i : order) {
         mlb_ctx* c = jobs[i].ctx;
         BatchPcgProblem b{};
@@ -340,7 +343,6 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
         b.maxit = o.pcg_maxit;
         b.st = c->pcg;
         hp.push_back(b);
-        idx.push_back(i);
     }
     mlb_status first = MLB_OK;
     BatchPcgProblem* dp = nullptr;
@@ -382,8 +384,7 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
         cudaStreamDestroy(ps);
     }
     if (dp) cudaFree(dp);
-    if (first == MLB_OK)
-        for (int i : idx) jobs[i].ctx->launches += 1;
+    const int64_t persistent = (first == MLB_OK && !hp.empty()) ? 1 : 0;
     g_batch_phase_ms[1] = ms_since(tp);
     tp = std::chrono::steady_clock::now();
     // phase 3: gamma, trend, predictions
@@ -392,7 +393,9 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
             cudaSetDevice(o.device);
             return finish_one(j);
         });
+    g_batch_launches = persistent;
     for (int i = 0; i < count; ++i) {
+        if (jobs[i].ctx) g_batch_launches += jobs[i].ctx->launches;
         probs[i].status = jobs[i].status;
         if (first == MLB_OK && jobs[i].status != MLB_OK) {
             first = jobs[i].status;
