@@ -2,12 +2,16 @@
 // Sec. 6.2) and the trend step beta = (X^T X)^{-1} X^T (Z - C gamma)
 // (eq. Spatial:eqn3).
 //
-// Vectors, inner products and updates are FP64.  The matrix-vector product is
-// a warp-per-row pass over the row panels of C~_W (HBM bound).  Inner
-// products are deterministic: every kernel writes per-block partial sums and
-// a one-block kernel adds them in a fixed order.  The scalars of the
-// iteration live on the device; the host only reads the "done" flag between
-// chunks of iterations, which are replayed as a captured CUDA graph.
+// Vectors, inner products and updates are FP64.  The matrix-vector product
+// streams the row panels of C~_W (HBM bound in FP32, FP64-pipe bound in FP64).
+// Inner products are deterministic: every CTA writes its partial sums and the
+// CTA that finishes last (a ticket count, no waiting) adds them in a fixed
+// order, so one iteration is two or three launches: the product (whose last
+// CTA forms alpha), the vector update (whose last CTA forms beta and the
+// stopping test, and p for short vectors) and, for long vectors, the p
+// update.  The scalars of the iteration live on the device; the host only
+// reads the "done" flag between chunks of iterations, which are replayed as a
+// captured CUDA graph.
 // Stopping test: ||r_k||_2 <= rtol ||Z_W||_2 on the unpreconditioned
 // residual r_k = Z_W - C~_W g_k (remark closing Sec. 6.2).
 #include <algorithm>
