@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--targets", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mse", type=int, default=0,
+                    help="time the kriging MSE at this many targets instead (one PCG solve each)")
     return ap.parse_args()
 
 
@@ -419,6 +421,42 @@ def run_batched(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_mse(args, rank, world, local_rank):
+    """Kriging MSE at K targets of the workload (the formula after eq.
+    Spatial): one multilevel PCG solve per target on the assembled C~_W.
+    Prints its own JSON line: MSE targets/s per precision."""
+    import torch
+    import paper_1701_00285_gb300 as pkg
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    P = workload(args, rank)
+    K = args.mse
+    tg = np.ascontiguousarray(P.targets[:K])
+    out = {}
+    for prec in ("mixed", "fp64"):
+        ctx = pkg.Context(prec, leaf_size=P.leaf_size, pcg_rtol=P.pcg_rtol, pcg_maxit=50000, device=local_rank)
+        ctx.build_basis(P.points, P.w)
+        ctx.assemble(P.nu, P.rho, P.nugget, P.tau_factor)
+        for _ in range(args.warmup):
+            ctx.mse(tg[:1])
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = ctx.mse(tg)
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, world, dev)
+        out[prec] = {"value": world * K / dt, "s": dt, "mse": m}
+        ctx.close()
+    line = {"metric": "kriging MSE at targets (one multilevel PCG solve each)", "value": out["mixed"]["value"],
+            "unit": "targets/s", "n_gpus": world, "targets": K, "higher_is_better": True, "scaling": "weak",
+            "dtype": "f32/f64", "data": "synthetic", "config": {"workload": describe(P)},
+            "fp64": {"value": out["fp64"]["value"]},
+            "mixed_vs_fp64_max_abs": float(np.max(np.abs(out["mixed"]["mse"] - out["fp64"]["mse"]))),
+            "mse_range": [float(out["fp64"]["mse"].min()), float(out["fp64"]["mse"].max())]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1701_00285_gb300 as pkg
@@ -510,6 +548,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "config4":
         run_batched(args, rank, world, local_rank)
+    elif args.mse:
+        run_mse(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

@@ -151,6 +151,16 @@ mlb_status mlb_predict_dev(mlb_ctx* ctx, const double* targets_dev, int64_t M, d
 mlb_status mlb_grad(mlb_ctx* ctx, const double* targets, int64_t M, const double* y_obs,
                     double* loss_out, double* dlogrho_out, double* dlognugget_out);
 
+/* Kriging mean squared error at M targets (the formula after eq. Spatial,
+ * unit variance): MSE(x0) = 1 + u^T (X^T C^{-1} X)^{-1} u - c^T C^{-1} c with
+ * u = X^T C^{-1} c - k(x0), c = c(x0), evaluated as 1 - c^T lambda - k^T mu
+ * from the saddle-point system [[C, X], [X^T, 0]] [lambda; mu] = [c; k]; one
+ * multilevel PCG solve on C~_W per target.  Requires mlb_assemble (not a
+ * solve).  targets: host M x d row-major; mse_out: host M.  The _dev form
+ * takes device buffers.  MLB_EBREAKDOWN / MLB_ENOCONV as for mlb_solve. */
+mlb_status mlb_mse(mlb_ctx* ctx, const double* targets, int64_t M, double* mse_out);
+mlb_status mlb_mse_dev(mlb_ctx* ctx, const double* targets_dev, int64_t M, double* out_dev);
+
 /* ---- many independent problems -------------------------------------------- */
 
 typedef struct {

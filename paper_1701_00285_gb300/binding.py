@@ -73,6 +73,8 @@ _SIGS = {
     "mlb_predict": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mlb_predict_dev": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mlb_grad": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
+    "mlb_mse": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "mlb_mse_dev": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mlb_batch_solve": (ctypes.c_int, [ctypes.POINTER(Opts), ctypes.POINTER(BatchProblem), ctypes.c_int,
                                        ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "mlb_batch_last_error": (ctypes.c_char_p, []),
@@ -255,6 +257,18 @@ class Context:
 
     def predict_dev(self, targets_ptr: int, M: int, out_ptr: int):
         self._check(lib().mlb_predict_dev(self._h, targets_ptr, M, out_ptr))
+
+    def mse(self, targets) -> np.ndarray:
+        """Kriging mean squared error at the targets (one PCG solve each)."""
+        tg = _f64(targets)
+        if tg.ndim != 2 or tg.shape[1] != self.d:
+            raise ValueError("targets must be (M, d)")
+        out = np.empty(tg.shape[0])
+        self._check(lib().mlb_mse(self._h, _ptr(tg), tg.shape[0], _ptr(out)))
+        return out
+
+    def mse_dev(self, targets_ptr: int, M: int, out_ptr: int):
+        self._check(lib().mlb_mse_dev(self._h, targets_ptr, M, out_ptr))
 
     def grad(self, targets, y_obs):
         tg = _f64(targets)

@@ -686,6 +686,37 @@ mlb_status mlb_kernel_sum(mlb_ctx* ctx, const double* targets, int64_t M, const 
                           [&](double* din, double* dout) { return kernel_sum_dev(ctx, din, M, akd, dout, false); });
 }
 
+mlb_status mlb_mse_dev(mlb_ctx* ctx, const double* targets_dev, int64_t M, double* out_dev) {
+    if (!ctx || !targets_dev || !out_dev || M < 1) return fail(ctx, MLB_EINVAL, "bad argument");
+    ctx->err.clear();
+    if (ctx->state < 2) return fail(ctx, MLB_ESTATE, "mlb_mse needs mlb_assemble first");
+    cudaSetDevice(ctx->opts.device);
+    return mse_dev(ctx, targets_dev, M, out_dev);
+}
+
+mlb_status mlb_mse(mlb_ctx* ctx, const double* targets, int64_t M, double* mse_out) {
+    if (!ctx || !targets || !mse_out || M < 1) return fail(ctx, MLB_EINVAL, "bad argument");
+    ctx->err.clear();
+    if (ctx->state < 2) return fail(ctx, MLB_ESTATE, "mlb_mse needs mlb_assemble first");
+    cudaSetDevice(ctx->opts.device);
+    double *tg = nullptr, *o = nullptr;
+    mlb_status s = MLB_OK;
+    if (cudaMalloc(&tg, sizeof(double) * M * ctx->d) != cudaSuccess || cudaMalloc(&o, sizeof(double) * M) != cudaSuccess)
+        s = fail(ctx, MLB_ENOMEM, "cudaMalloc failed");
+    if (s == MLB_OK &&
+        cudaMemcpyAsync(tg, targets, sizeof(double) * M * ctx->d, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        s = fail(ctx, MLB_ECUDA, "copy of targets failed");
+    if (s == MLB_OK) s = mse_dev(ctx, tg, M, o);
+    if (s == MLB_OK) {
+        cudaError_t e = cudaMemcpyAsync(mse_out, o, sizeof(double) * M, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) s = cuda_fail(ctx, e, "MSE copy");
+    }
+    cudaFree(tg);
+    cudaFree(o);
+    return s;
+}
+
 mlb_status mlb_grad(mlb_ctx* ctx, const double* targets, int64_t M, const double* y_obs, double* loss_out,
                     double* dlogrho_out, double* dlognugget_out) {
     if (!ctx || !targets || !y_obs || M < 1) return fail(ctx, MLB_EINVAL, "bad argument");

@@ -220,3 +220,116 @@ mlb_status grad_dev(mlb_ctx* ctx, const double* tg, int64_t M, const double* y, 
 }
 
 }  // namespace mlb
+
+namespace mlb {
+
+// part[b][m] = sum over the block's rows of X[r][m] v[r]
+__global__ void xtv_kernel(int64_t N, int p, const double* __restrict__ X, const double* __restrict__ v,
+                           int64_t chunk, double* __restrict__ part) {
+    const int64_t r0 = blockIdx.x * chunk, r1 = min(N, r0 + chunk);
+    for (int m = threadIdx.x; m < p; m += blockDim.x) {
+        double acc = 0.0;
+        for (int64_t r = r0; r < r1; ++r) acc += X[r * p + m] * v[r];
+        part[(int64_t)blockIdx.x * p + m] = acc;
+    }
+}
+
+// out = 1 - a.lambda - b.mu from the partials of a.lambda and the p-vectors b, mu
+__global__ void mse_finish_kernel(const double* pa, int nb, const double* b, const double* mu, int p, double* out) {
+    if (threadIdx.x) return;
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += pa[i];
+    double t = 0.0;
+    for (int m = 0; m < p; ++m) t += b[m] * mu[m];
+    *out = 1.0 - s - t;
+}
+
+// Kriging mean squared error at each target (the formula after eq. Spatial,
+// unit variance): MSE(x0) = 1 - c^T lambda - k^T mu, where [lambda; mu] solves
+// the saddle-point system [[C, X], [X^T, 0]] [lambda; mu] = [c(x0); k(x0)]
+// (substituting lambda = C^{-1}(c - X mu) and X^T lambda = k gives the
+// printed 1 + u^T (X^T C^{-1} X)^{-1} u - c^T C^{-1} c).  Solved the
+// multilevel way, one target at a time:
+//   lambda_0 = X (X^T X)^{-1} k,  C~_W lambda_W = W (c - C lambda_0),
+//   lambda = lambda_0 + W^T lambda_W,  mu = (X^T X)^{-1} X^T (c - C lambda).
+// The kernel sums run at the one-shot accuracy (double-float on the mixed
+// path); the PCG is the context's (FP32 or FP64 C~_W).
+mlb_status mse_dev(mlb_ctx* ctx, const double* tg, int64_t M, double* out) {
+    cudaStream_t st = ctx->stream;
+    const int64_t N = ctx->N, nw = ctx->nwav;
+    const int p = ctx->p, d = ctx->d;
+    Arena tmp;
+    double* a = (double*)dalloc(ctx, tmp, sizeof(double) * N);
+    double* l0 = (double*)dalloc(ctx, tmp, sizeof(double) * N);
+    double* Kl = (double*)dalloc(ctx, tmp, sizeof(double) * N);
+    double* lam = (double*)dalloc(ctx, tmp, sizeof(double) * N);
+    double* t2 = (double*)dalloc(ctx, tmp, sizeof(double) * N);
+    double* rw = (double*)dalloc(ctx, tmp, sizeof(double) * nw);
+    double* lw = (double*)dalloc(ctx, tmp, sizeof(double) * nw);
+    double* small = (double*)dalloc(ctx, tmp, sizeof(double) * (4 * 128 + 8));
+    double* box = (double*)dalloc(ctx, tmp, sizeof(double) * 2 * kMaxDim);
+    double* part = (double*)dalloc(ctx, tmp, sizeof(double) * (size_t)(kRedBlocks * 128 + kRedBlocks));
+    if (!a || !l0 || !Kl || !lam || !t2 || !rw || !lw || !small || !box || !part) {
+        tmp.release();
+        return fail(ctx, MLB_ENOMEM, "MSE work buffers");
+    }
+    double* one = small;            // the weight 1 of a single source
+    double* b = small + 8;          // k(x0)
+    double* c = b + 128;            // (X^T X)^{-1} k(x0)
+    double* mu = c + 128;
+    double* pa = part + (size_t)kRedBlocks * 128;
+    double hb[2 * kMaxDim + 1];
+    for (int q = 0; q < d; ++q) {
+        hb[q] = ctx->box_lo[q];
+        hb[kMaxDim + q] = ctx->box_hi[q];
+    }
+    hb[2 * kMaxDim] = 1.0;
+    const int64_t chunk = (N + kRedBlocks - 1) / kRedBlocks;
+    mlb_status s = MLB_OK;
+    do {
+        if (cudaMemcpyAsync(box, hb, sizeof(double) * 2 * kMaxDim, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(one, hb + 2 * kMaxDim, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            s = fail(ctx, MLB_ECUDA, "copy");
+            break;
+        }
+        for (int64_t k = 0; k < M && s == MLB_OK; ++k) {
+            const double* x0 = tg + k * d;
+            // c(x0) at every data point (kd order): a kernel sum with one source of weight 1
+            if ((s = kernel_sum_general(ctx, nullptr, N, x0, 1, one, a, false, false, true)) != MLB_OK) break;
+            // b = k(x0), c = (X^T X)^{-1} b, lambda_0 = X c
+            trend_adjoint_kernel<<<1, 32, sizeof(double) * 32 * p, st>>>(1, d, p, x0, one, ctx->alpha, box,
+                                                                         box + kMaxDim, b);
+            small_solve_kernel<<<1, 32, 0, st>>>(b, 1, p, ctx->XtXf, c);
+            xc_kernel<<<nblk(N), 256, 0, st>>>(N, p, ctx->X, c, l0);
+            MLB_CHECK_LAUNCH(ctx, "MSE trend part");
+            ctx->launches += 2;
+            // C~_W lambda_W = W (c(x0) - C lambda_0)
+            if ((s = kernel_sum_general(ctx, nullptr, N, nullptr, N, l0, Kl, false, false, true)) != MLB_OK) break;
+            rhs_kernel<<<nblk(N), 256, 0, st>>>(N, a, Kl, l0, ctx->theta.nugget, t2);
+            MLB_CHECK_LAUNCH(ctx, "rhs_kernel");
+            if ((s = apply_W_dev(ctx, t2, rw)) != MLB_OK) break;
+            mlb_info ai{};
+            if ((s = pcg_run(ctx, rw, lw, &ai)) != MLB_OK) break;
+            if ((s = apply_Wt_dev(ctx, lw, lam)) != MLB_OK) break;
+            add_kernel<<<nblk(N), 256, 0, st>>>(N, l0, lam);
+            MLB_CHECK_LAUNCH(ctx, "add_kernel");
+            // mu = (X^T X)^{-1} X^T (c(x0) - C lambda - eta lambda)
+            if ((s = kernel_sum_general(ctx, nullptr, N, nullptr, N, lam, Kl, false, false, true)) != MLB_OK) break;
+            rhs_kernel<<<nblk(N), 256, 0, st>>>(N, a, Kl, lam, ctx->theta.nugget, t2);
+            xtv_kernel<<<kRedBlocks, 32, 0, st>>>(N, p, ctx->X, t2, chunk, part);
+            small_solve_kernel<<<1, 32, 0, st>>>(part, kRedBlocks, p, ctx->XtXf, mu);
+            dot_kernel<<<kRedBlocks, 256, 0, st>>>(N, a, lam, pa);
+            mse_finish_kernel<<<1, 32, 0, st>>>(pa, kRedBlocks, b, mu, p, out + k);
+            MLB_CHECK_LAUNCH(ctx, "MSE reductions");
+            ctx->launches += 4;
+        }
+        if (s != MLB_OK) break;
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(ctx, e, "MSE");
+    } while (0);
+    cudaStreamSynchronize(st);
+    tmp.release();
+    return s;
+}
+
+}  // namespace mlb

@@ -200,5 +200,6 @@ mlb_status tune_kernel_sum(mlb_ctx* ctx);
 mlb_status pcg_run(mlb_ctx* ctx, const double* b, double* x, mlb_info* info);
 // grad.cu
 mlb_status grad_dev(mlb_ctx* ctx, const double* targets, int64_t M, const double* y, double* out3);
+mlb_status mse_dev(mlb_ctx* ctx, const double* targets, int64_t M, double* out);
 
 }  // namespace mlb

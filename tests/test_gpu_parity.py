@@ -434,3 +434,35 @@ def test_batch_solve_mixed_sizes_dense_oracle(pkg, prec, tol):
         assert s == 0 and its > 0, q.name
         ref = dense.dense_blup(q.points, q.Z, q.targets[:150], q.w, q.nu, q.rho, q.nugget)
         assert rel(y, ref["yhat"]) < tol, (q.name, prec)
+
+
+# ---- kriging mean squared error ---------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("mixed", 1e-5)])
+def test_mse_matches_dense_oracle(pkg, prec, tol):
+    """MSE at targets and at data points (tau = infinity) against the dense
+    oracle's formula; absolute error in units of the process variance."""
+    P = wl.small_problem(600, 1500, 2, 1, nu=1.5, rho=0.3, nugget=1e-4, leaf_size=32, M=40)
+    tg = np.vstack([P.points[:5], P.targets[:35]])
+    ref = dense.mse_at(P.points, tg, P.w, P.nu, P.rho, P.nugget)
+    ctx = ctx_for(pkg, P, prec, rtol=1e-12, pcg_maxit=50000)
+    with pytest.raises(pkg.MLBError):
+        ctx.mse(tg)                                     # before mlb_assemble: MLB_ESTATE
+    ctx.assemble(P.nu, P.rho, P.nugget, math.inf)
+    got = ctx.mse(tg)
+    assert np.max(np.abs(got - ref)) < tol
+    assert np.all(got[:5] < 1e-3) and np.all(got > -tol)
+
+
+def test_mse_matrix_free_matches_assembled(pkg):
+    """The same MSE through the three-step product (no assembled C~_W)."""
+    P = wl.small_problem(601, 900, 3, 1, nu=2.5, rho=0.4, nugget=1e-4, leaf_size=32, M=8)
+    got = {}
+    for mf in (False, True):
+        ctx = pkg.Context("fp64", leaf_size=32, pcg_rtol=1e-12, pcg_maxit=50000, matrix_free=mf, precond=not mf)
+        ctx.build_basis(P.points, P.w)
+        ctx.assemble(P.nu, P.rho, P.nugget, math.inf)
+        got[mf] = ctx.mse(P.targets)
+    ref = dense.mse_at(P.points, P.targets, P.w, P.nu, P.rho, P.nugget)
+    assert np.max(np.abs(got[False] - ref)) < 1e-8
+    assert np.max(np.abs(got[True] - ref)) < 1e-8

@@ -139,3 +139,35 @@ def test_mse_nonnegative_and_zero_at_data():
     m = dense.mse_at(P.points, np.vstack([P.points[:5], P.targets]), 1, 1.5, 0.3, 0.0)
     assert np.all(m > -1e-8)
     np.testing.assert_allclose(m[:5], 0.0, atol=1e-7)
+
+
+def test_mse_single_point_closed_form():
+    """One observation, constant trend (w = 0), no nugget: the kriging weight
+    is forced to 1 by the unbiasedness constraint, so the error variance is
+    Var(Z(x0) - Z(x1)) = 2 - 2 phi(|x0 - x1|)."""
+    x1 = np.array([[0.3, 0.7]])
+    tg = np.array([[0.3, 0.7], [0.5, 0.5], [0.9, 0.1], [3.0, -2.0]])
+    for nu in (0.5, 1.5, 2.5):
+        m = dense.mse_at(x1, tg, 0, nu, 0.4, 0.0)
+        r = np.linalg.norm(tg - x1, axis=1)
+        np.testing.assert_allclose(m, 2.0 - 2.0 * matern.matern(r, nu, 0.4), rtol=1e-12, atol=1e-14)
+
+
+def test_mse_equals_error_variance_of_the_kriging_weights():
+    """The MSE formula against its definition: with the weights w0 of the
+    predictor Z-hat(x0) = w0^T Z (from the saddle-point system with right-hand
+    side [c(x0); k(x0)]), the error variance is phi(0) - 2 w0^T c + w0^T C w0,
+    where C carries the nugget and c(x0) does not."""
+    P = wl.small_problem(29, 90, 2, 1, nugget=1e-3, leaf_size=10)
+    lo, hi = design.box(P.points)
+    X = design.design_matrix(P.points, 1, lo, hi)
+    C = matern.covariance(P.points, 1.5, 0.3, 1e-3)
+    N, p = X.shape
+    K = np.zeros((N + p, N + p))
+    K[:N, :N], K[:N, N:], K[N:, :N] = C, X, X.T
+    tg = P.targets[:6]
+    c0 = matern.kernel_matrix(P.points, tg, 1.5, 0.3)
+    k0 = design.design_matrix(tg, 1, lo, hi).T
+    w0 = np.linalg.solve(K, np.vstack([c0, k0]))[:N]
+    var = 1.0 - 2.0 * np.einsum("ik,ik->k", w0, c0) + np.einsum("ik,ik->k", w0, C @ w0)
+    np.testing.assert_allclose(dense.mse_at(P.points, tg, 1, 1.5, 0.3, 1e-3), var, rtol=1e-9, atol=1e-12)
