@@ -159,6 +159,19 @@ mlb_status mlb_grad(mlb_ctx* ctx, const double* targets, int64_t M, const double
  * solve).  targets: host M x d row-major; mse_out: host M.  The _dev form
  * takes device buffers.  MLB_EBREAKDOWN / MLB_ENOCONV as for mlb_solve. */
 mlb_status mlb_mse(mlb_ctx* ctx, const double* targets, int64_t M, double* mse_out);
+
+/* Multilevel log-likelihood (Sec. 5.1, the reduced likelihood of the full
+ * transform): l_W = -(N~/2) log(2 pi) - (1/2) log det C~_W - (1/2) Z_W^T
+ * C~_W^{-1} Z_W, with Z_W = W Z and N~ = N - p.  The quadratic form comes from
+ * the PCG solve; log det C~_W is estimated by stochastic Lanczos quadrature
+ * (steps Lanczos steps, 1..100, fully reorthogonalised) over nprobe probe
+ * vectors z_i that the caller draws in the data space (host, nprobe x N, caller
+ * order; W z_i enters the Lanczos recurrence), e.g. Rademacher entries.  With
+ * nprobe = 0 the log-determinant is not estimated and reported as 0.  Z: host,
+ * N, caller order.  out3 = {l_W, log det estimate, quadratic form} (host).
+ * Requires mlb_assemble.  The paper has no stochastic estimator: it uses a
+ * sparse Cholesky factorisation. */
+mlb_status mlb_loglik(mlb_ctx* ctx, const double* Z, const double* probes, int nprobe, int steps, double* out3);
 mlb_status mlb_mse_dev(mlb_ctx* ctx, const double* targets_dev, int64_t M, double* out_dev);
 
 /* ---- many independent problems -------------------------------------------- */

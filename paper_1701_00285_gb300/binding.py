@@ -74,6 +74,7 @@ _SIGS = {
     "mlb_predict_dev": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mlb_grad": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
     "mlb_mse": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "mlb_loglik": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
     "mlb_mse_dev": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mlb_batch_solve": (ctypes.c_int, [ctypes.POINTER(Opts), ctypes.POINTER(BatchProblem), ctypes.c_int,
                                        ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -257,6 +258,22 @@ class Context:
 
     def predict_dev(self, targets_ptr: int, M: int, out_ptr: int):
         self._check(lib().mlb_predict_dev(self._h, targets_ptr, M, out_ptr))
+
+    def loglik(self, Z, probes=None, steps: int = 30):
+        """(l_W, log det C~_W, Z_W^T C~_W^{-1} Z_W): the multilevel log-likelihood
+        with the log-determinant estimated by stochastic Lanczos quadrature over
+        the probe rows (data space, N entries each; None: no estimate)."""
+        Z = _f64(Z, (self.N,))
+        if probes is None:
+            pr, m = None, 0
+        else:
+            pr = _f64(probes)
+            if pr.ndim != 2 or pr.shape[1] != self.N:
+                raise ValueError("probes must be (m, N)")
+            m = pr.shape[0]
+        out = np.empty(3)
+        self._check(lib().mlb_loglik(self._h, _ptr(Z), _ptr(pr) if pr is not None else None, m, steps, _ptr(out)))
+        return float(out[0]), float(out[1]), float(out[2])
 
     def mse(self, targets) -> np.ndarray:
         """Kriging mean squared error at the targets (one PCG solve each)."""

@@ -466,3 +466,27 @@ def test_mse_matrix_free_matches_assembled(pkg):
     ref = dense.mse_at(P.points, P.targets, P.w, P.nu, P.rho, P.nugget)
     assert np.max(np.abs(got[False] - ref)) < 1e-8
     assert np.max(np.abs(got[True] - ref)) < 1e-8
+
+
+# ---- multilevel log-likelihood ------------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_loglik_matches_oracle(pkg, prec, tol):
+    """Quadratic form against the oracle's exact solve; the stochastic Lanczos
+    log-determinant against the oracle's estimate with the same probes and
+    steps (the same recurrence, rotated within each cell's wavelet block);
+    and the likelihood formula."""
+    from oracle import loglik as olog
+    P = wl.small_problem(610, 700, 2, 1, nu=1.5, rho=0.3, nugget=1e-3, leaf_size=32, M=8)
+    B = mlblup.setup(P.points, P.w, P.leaf_size)
+    probes = np.random.default_rng(5).choice([-1.0, 1.0], size=(6, P.N))
+    _, ld_ref, q_ref = olog.multilevel_loglik(B, P.points, P.Z, P.nu, P.rho, P.nugget, probes=probes, steps=20)
+    ctx = ctx_for(pkg, P, prec, rtol=1e-12, pcg_maxit=50000)
+    ctx.assemble(P.nu, P.rho, P.nugget, math.inf)
+    l, ld, q = ctx.loglik(P.Z, probes, 20)
+    assert abs(q - q_ref) < tol * abs(q_ref)
+    assert abs(ld - ld_ref) < tol * max(1.0, abs(ld_ref))
+    n = P.N - B.p
+    assert abs(l + 0.5 * (n * math.log(2 * math.pi) + ld + q)) < 1e-12 * abs(l)
+    l0, ld0, q0 = ctx.loglik(P.Z)                       # no probes: no estimate
+    assert ld0 == 0.0 and abs(q0 - q) < 1e-9 * abs(q)
