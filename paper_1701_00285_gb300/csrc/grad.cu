@@ -253,29 +253,35 @@ __global__ void mse_finish_kernel(const double* pa, int nb, const double* b, con
 //   lambda_0 = X (X^T X)^{-1} k,  C~_W lambda_W = W (c - C lambda_0),
 //   lambda = lambda_0 + W^T lambda_W,  mu = (X^T X)^{-1} X^T (c - C lambda).
 // The kernel sums run at the one-shot accuracy (double-float on the mixed
-// path); the PCG is the context's (FP32 or FP64 C~_W).
+// path); the PCG is the context's (FP32 or FP64 C~_W), with kRhs targets per
+// pass over the FP32 panels.
 mlb_status mse_dev(mlb_ctx* ctx, const double* tg, int64_t M, double* out) {
     cudaStream_t st = ctx->stream;
     const int64_t N = ctx->N, nw = ctx->nwav;
     const int p = ctx->p, d = ctx->d;
+    // on the FP32 panels kRhs targets share each pass over C~_W (one PCG
+    // recurrence per target, one product for all); otherwise one at a time
+    const bool multi = ctx->pan.vals32 && !ctx->opts.matrix_free && ctx->pan.nwork > 0;
+    const int R = multi ? kRhs : 1;
     Arena tmp;
-    double* a = (double*)dalloc(ctx, tmp, sizeof(double) * N);
-    double* l0 = (double*)dalloc(ctx, tmp, sizeof(double) * N);
+    double* A = (double*)dalloc(ctx, tmp, sizeof(double) * R * N);      // c(x0) per slot
+    double* L0 = (double*)dalloc(ctx, tmp, sizeof(double) * R * N);     // lambda_0 per slot
+    double* Bk = (double*)dalloc(ctx, tmp, sizeof(double) * R * 128);   // k(x0) per slot
+    double* RW = (double*)dalloc(ctx, tmp, sizeof(double) * R * nw);    // right-hand sides W(c - C lambda_0)
+    double* LW = (double*)dalloc(ctx, tmp, sizeof(double) * R * nw);    // lambda_W
     double* Kl = (double*)dalloc(ctx, tmp, sizeof(double) * N);
     double* lam = (double*)dalloc(ctx, tmp, sizeof(double) * N);
     double* t2 = (double*)dalloc(ctx, tmp, sizeof(double) * N);
-    double* rw = (double*)dalloc(ctx, tmp, sizeof(double) * nw);
-    double* lw = (double*)dalloc(ctx, tmp, sizeof(double) * nw);
-    double* small = (double*)dalloc(ctx, tmp, sizeof(double) * (4 * 128 + 8));
+    double* small = (double*)dalloc(ctx, tmp, sizeof(double) * (3 * 128 + 8));
     double* box = (double*)dalloc(ctx, tmp, sizeof(double) * 2 * kMaxDim);
     double* part = (double*)dalloc(ctx, tmp, sizeof(double) * (size_t)(kRedBlocks * 128 + kRedBlocks));
-    if (!a || !l0 || !Kl || !lam || !t2 || !rw || !lw || !small || !box || !part) {
+    double* work = multi ? (double*)dalloc(ctx, tmp, sizeof(double) * pcg_multi_work_doubles(ctx)) : nullptr;
+    if (!A || !L0 || !Bk || !RW || !LW || !Kl || !lam || !t2 || !small || !box || !part || (multi && !work)) {
         tmp.release();
         return fail(ctx, MLB_ENOMEM, "MSE work buffers");
     }
     double* one = small;            // the weight 1 of a single source
-    double* b = small + 8;          // k(x0)
-    double* c = b + 128;            // (X^T X)^{-1} k(x0)
+    double* c = small + 8;          // (X^T X)^{-1} k(x0)
     double* mu = c + 128;
     double* pa = part + (size_t)kRedBlocks * 128;
     double hb[2 * kMaxDim + 1];
@@ -292,36 +298,50 @@ mlb_status mse_dev(mlb_ctx* ctx, const double* tg, int64_t M, double* out) {
             s = fail(ctx, MLB_ECUDA, "copy");
             break;
         }
-        for (int64_t k = 0; k < M && s == MLB_OK; ++k) {
-            const double* x0 = tg + k * d;
-            // c(x0) at every data point (kd order): a kernel sum with one source of weight 1
-            if ((s = kernel_sum_general(ctx, nullptr, N, x0, 1, one, a, false, false, true)) != MLB_OK) break;
-            // b = k(x0), c = (X^T X)^{-1} b, lambda_0 = X c
-            trend_adjoint_kernel<<<1, 32, sizeof(double) * 32 * p, st>>>(1, d, p, x0, one, ctx->alpha, box,
-                                                                         box + kMaxDim, b);
-            small_solve_kernel<<<1, 32, 0, st>>>(b, 1, p, ctx->XtXf, c);
-            xc_kernel<<<nblk(N), 256, 0, st>>>(N, p, ctx->X, c, l0);
-            MLB_CHECK_LAUNCH(ctx, "MSE trend part");
-            ctx->launches += 2;
+        for (int64_t k0 = 0; k0 < M && s == MLB_OK; k0 += R) {
+            // per slot: c(x0), k(x0), lambda_0 = X (X^T X)^{-1} k(x0) and the
+            // right-hand side W (c(x0) - C lambda_0); slots past M repeat the
+            // last target and are not reported
+            for (int r = 0; r < R && s == MLB_OK; ++r) {
+                const double* x0 = tg + std::min<int64_t>(k0 + r, M - 1) * d;
+                double* a = A + (int64_t)r * N;
+                double* l0 = L0 + (int64_t)r * N;
+                double* b = Bk + r * 128;
+                if ((s = kernel_sum_general(ctx, nullptr, N, x0, 1, one, a, false, false, true)) != MLB_OK) break;
+                trend_adjoint_kernel<<<1, 32, sizeof(double) * 32 * p, st>>>(1, d, p, x0, one, ctx->alpha, box,
+                                                                             box + kMaxDim, b);
+                small_solve_kernel<<<1, 32, 0, st>>>(b, 1, p, ctx->XtXf, c);
+                xc_kernel<<<nblk(N), 256, 0, st>>>(N, p, ctx->X, c, l0);
+                MLB_CHECK_LAUNCH(ctx, "MSE trend part");
+                ctx->launches += 2;
+                if ((s = kernel_sum_general(ctx, nullptr, N, nullptr, N, l0, Kl, false, false, true)) != MLB_OK) break;
+                rhs_kernel<<<nblk(N), 256, 0, st>>>(N, a, Kl, l0, ctx->theta.nugget, t2);
+                MLB_CHECK_LAUNCH(ctx, "rhs_kernel");
+                if ((s = apply_W_dev(ctx, t2, RW + (int64_t)r * nw)) != MLB_OK) break;
+            }
+            if (s != MLB_OK) break;
             // C~_W lambda_W = W (c(x0) - C lambda_0)
-            if ((s = kernel_sum_general(ctx, nullptr, N, nullptr, N, l0, Kl, false, false, true)) != MLB_OK) break;
-            rhs_kernel<<<nblk(N), 256, 0, st>>>(N, a, Kl, l0, ctx->theta.nugget, t2);
-            MLB_CHECK_LAUNCH(ctx, "rhs_kernel");
-            if ((s = apply_W_dev(ctx, t2, rw)) != MLB_OK) break;
-            mlb_info ai{};
-            if ((s = pcg_run(ctx, rw, lw, &ai)) != MLB_OK) break;
-            if ((s = apply_Wt_dev(ctx, lw, lam)) != MLB_OK) break;
-            add_kernel<<<nblk(N), 256, 0, st>>>(N, l0, lam);
-            MLB_CHECK_LAUNCH(ctx, "add_kernel");
-            // mu = (X^T X)^{-1} X^T (c(x0) - C lambda - eta lambda)
-            if ((s = kernel_sum_general(ctx, nullptr, N, nullptr, N, lam, Kl, false, false, true)) != MLB_OK) break;
-            rhs_kernel<<<nblk(N), 256, 0, st>>>(N, a, Kl, lam, ctx->theta.nugget, t2);
-            xtv_kernel<<<kRedBlocks, 32, 0, st>>>(N, p, ctx->X, t2, chunk, part);
-            small_solve_kernel<<<1, 32, 0, st>>>(part, kRedBlocks, p, ctx->XtXf, mu);
-            dot_kernel<<<kRedBlocks, 256, 0, st>>>(N, a, lam, pa);
-            mse_finish_kernel<<<1, 32, 0, st>>>(pa, kRedBlocks, b, mu, p, out + k);
-            MLB_CHECK_LAUNCH(ctx, "MSE reductions");
-            ctx->launches += 4;
+            if (multi) {
+                if ((s = pcg_run_multi(ctx, RW, LW, work, nullptr)) != MLB_OK) break;
+            } else {
+                mlb_info ai{};
+                if ((s = pcg_run(ctx, RW, LW, &ai)) != MLB_OK) break;
+            }
+            for (int r = 0; r < R && k0 + r < M && s == MLB_OK; ++r) {
+                const double* a = A + (int64_t)r * N;
+                // lambda = lambda_0 + W^T lambda_W; mu = (X^T X)^{-1} X^T (c(x0) - C lambda - eta lambda)
+                if ((s = apply_Wt_dev(ctx, LW + (int64_t)r * nw, lam)) != MLB_OK) break;
+                add_kernel<<<nblk(N), 256, 0, st>>>(N, L0 + (int64_t)r * N, lam);
+                MLB_CHECK_LAUNCH(ctx, "add_kernel");
+                if ((s = kernel_sum_general(ctx, nullptr, N, nullptr, N, lam, Kl, false, false, true)) != MLB_OK) break;
+                rhs_kernel<<<nblk(N), 256, 0, st>>>(N, a, Kl, lam, ctx->theta.nugget, t2);
+                xtv_kernel<<<kRedBlocks, 32, 0, st>>>(N, p, ctx->X, t2, chunk, part);
+                small_solve_kernel<<<1, 32, 0, st>>>(part, kRedBlocks, p, ctx->XtXf, mu);
+                dot_kernel<<<kRedBlocks, 256, 0, st>>>(N, a, lam, pa);
+                mse_finish_kernel<<<1, 32, 0, st>>>(pa, kRedBlocks, Bk + r * 128, mu, p, out + k0 + r);
+                MLB_CHECK_LAUNCH(ctx, "MSE reductions");
+                ctx->launches += 4;
+            }
         }
         if (s != MLB_OK) break;
         cudaError_t e = cudaStreamSynchronize(st);

@@ -198,6 +198,10 @@ mlb_status kernel_sum_general(mlb_ctx* ctx, const double* targets, int64_t M, co
 mlb_status tune_kernel_sum(mlb_ctx* ctx);
 // solve.cu: PCG on C~_W x = b (nwav vectors on the device)
 mlb_status pcg_run(mlb_ctx* ctx, const double* b, double* x, mlb_info* info);
+// kRhs simultaneous PCG solves on the FP32 panels (one pass over C~_W per iteration)
+constexpr int kRhs = 4;
+size_t pcg_multi_work_doubles(const mlb_ctx* ctx);
+mlb_status pcg_run_multi(mlb_ctx* ctx, const double* b, double* x, double* work, int* iters);
 // grad.cu
 mlb_status grad_dev(mlb_ctx* ctx, const double* targets, int64_t M, const double* y, double* out3);
 mlb_status mse_dev(mlb_ctx* ctx, const double* targets, int64_t M, double* out);

@@ -701,4 +701,355 @@ mlb_status trend_dev(mlb_ctx* ctx, const double* Z_kd) {
     return MLB_OK;
 }
 
+// ---- several right-hand sides at once (kriging MSE) ---------------------------
+//
+// kRhs independent diagonally preconditioned CG recurrences on the same FP32
+// C~_W, sharing one pass over the panels per iteration: every value loaded
+// feeds kRhs products, so the HBM traffic of an iteration is that of one
+// product.  Vectors are stored right-hand side after right-hand side (kRhs x n).
+// Each recurrence has its own scalars and stopping test; one that has stopped
+// is carried along unchanged until all have.
+
+__device__ __forceinline__ bool all_done(const PcgState* st) {
+    bool d = true;
+#pragma unroll
+    for (int r = 0; r < kRhs; ++r) d = d && st[r].done;
+    return d;
+}
+
+__global__ void __launch_bounds__(256, 2) spmm_panel_f32_kernel(Panels pan, const float* __restrict__ vals,
+                                                             const int* __restrict__ kcell,
+                                                             const int64_t* __restrict__ wOff,
+                                                             const double* __restrict__ x, int64_t nwav,
+                                                             double* __restrict__ ypart, double* __restrict__ part,
+                                                             PcgState* st) {
+    if (all_done(st)) return;
+    constexpr int CH = 256;
+    constexpr int QR = kItemRows / 8;
+    __shared__ __align__(16) float xh[2][kRhs][CH];
+    __shared__ __align__(16) float xl[2][kRhs][CH];
+    __shared__ double red[8][kRhs];
+    const int4 wk = pan.work[blockIdx.x];
+    const int g = wk.x;
+    const int rows = min(kItemRows, kcell[g] - wk.y);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nn = pan.ncols[g];
+    const int cb = wk.z;
+    const int n = min((int)nn, cb + kSegCols);
+    const int* ci = pan.colidx + pan.colOff[g];
+    const float* v0 = vals + pan.valOff[g] + (int64_t)wk.y * nn;
+    const int64_t r0 = wOff[g] + wk.y;
+    const int nq = min(QR, (rows - warp + 7) / 8);
+    float acc[QR][kRhs], err[QR][kRhs];
+#pragma unroll
+    for (int q = 0; q < QR; ++q)
+#pragma unroll
+        for (int r = 0; r < kRhs; ++r) acc[q][r] = err[q][r] = 0.0f;
+    if (threadIdx.x < min(CH, n - cb)) {
+        const int c = ci[cb + threadIdx.x];
+#pragma unroll
+        for (int r = 0; r < kRhs; ++r) {
+            const double xv = x[r * nwav + c];
+            const float h = (float)xv;
+            xh[0][r][threadIdx.x] = h;
+            xl[0][r][threadIdx.x] = (float)(xv - (double)h);
+        }
+    }
+    __syncthreads();
+    int buf = 0;
+    for (int c0 = cb; c0 < n; c0 += CH) {
+        const int m = min(CH, n - c0);
+        const int cn = c0 + CH + threadIdx.x;
+        const int pc = c0 + CH;
+        if (threadIdx.x < rows && pc < n)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(v0 + (int64_t)threadIdx.x * nn + pc),
+                         "r"((unsigned)(min(CH, n - pc) * 4))
+                         : "memory");
+        double xn[kRhs];
+        if (cn < n) {
+            const int c = ci[cn];
+#pragma unroll
+            for (int r = 0; r < kRhs; ++r) xn[r] = x[r * nwav + c];
+        }
+        if (m == CH) {
+            float4 v[QR][2];
+#pragma unroll
+            for (int q = 0; q < QR; ++q) {
+                const int rr = min(warp + 8 * q, rows - 1);
+                const float* row = v0 + (int64_t)rr * nn + c0 + 4 * lane;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) v[q][u] = *reinterpret_cast<const float4*>(row + 128 * u);
+            }
+#pragma unroll
+            for (int r = 0; r < kRhs; ++r) {
+#pragma unroll
+                for (int q = 0; q < QR; ++q) {
+                    if (q < nq) {
+                        float a = 0.0f;
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int j = 4 * lane + 128 * u;
+                            const float4 h = *reinterpret_cast<const float4*>(&xh[buf][r][j]);
+                            const float4 l = *reinterpret_cast<const float4*>(&xl[buf][r][j]);
+                            a += v[q][u].x * h.x + v[q][u].y * h.y + v[q][u].z * h.z + v[q][u].w * h.w;
+                            a += v[q][u].x * l.x + v[q][u].y * l.y + v[q][u].z * l.z + v[q][u].w * l.w;
+                        }
+                        sum2_add(acc[q][r], err[q][r], a);
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < QR; ++q) {
+                if (q < nq) {
+                    const float* row = v0 + (int64_t)(warp + 8 * q) * nn + c0;
+#pragma unroll
+                    for (int r = 0; r < kRhs; ++r) {
+                        const float* sh = xh[buf][r];
+                        const float* sl = xl[buf][r];
+                        float a = 0.0f;
+                        for (int j = 4 * lane; j < m; j += 128) {
+                            const float4 vv = *reinterpret_cast<const float4*>(row + j);
+                            a += vv.x * (sh[j] + sl[j]) + vv.y * (sh[j + 1] + sl[j + 1]) +
+                                 vv.z * (sh[j + 2] + sl[j + 2]) + vv.w * (sh[j + 3] + sl[j + 3]);
+                        }
+                        sum2_add(acc[q][r], err[q][r], a);
+                    }
+                }
+            }
+        }
+        if (cn < n) {
+#pragma unroll
+            for (int r = 0; r < kRhs; ++r) {
+                const float h = (float)xn[r];
+                xh[buf ^ 1][r][threadIdx.x] = h;
+                xl[buf ^ 1][r][threadIdx.x] = (float)(xn[r] - (double)h);
+            }
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+    double dotp[kRhs];
+#pragma unroll
+    for (int r = 0; r < kRhs; ++r) dotp[r] = 0.0;
+#pragma unroll
+    for (int q = 0; q < QR; ++q) {
+        const int row = warp + 8 * q;
+#pragma unroll
+        for (int r = 0; r < kRhs; ++r) {
+            double a = (double)acc[q][r] + (double)err[q][r];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0 && q < nq) {
+                ypart[((int64_t)r * pan.nsegMax + wk.w) * nwav + r0 + row] = a;
+                dotp[r] += x[r * nwav + r0 + row] * a;
+            }
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int r = 0; r < kRhs; ++r) red[warp][r] = dotp[r];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int r = 0; r < kRhs; ++r) {
+            double s2 = 0.0;
+            for (int i = 0; i < 8; ++i) s2 += red[i][r];
+            part[(int64_t)r * gridDim.x + blockIdx.x] = s2;
+        }
+    if (draw_last_ticket(st))
+        for (int r = 0; r < kRhs; ++r)
+            if (!st[r].done) pcg_alpha_finish(part + (int64_t)r * gridDim.x, gridDim.x, st + r);
+}
+
+// x_r += alpha_r p_r, r_r -= alpha_r q_r (q_r from the segment partials),
+// z_r = P^{-1} r_r and the partials of r_r.r_r and r_r.z_r; the last CTA forms
+// beta_r and the stopping test of every recurrence still running.
+__global__ void pcg_update_multi_kernel(int64_t n, PcgState* st, const double* __restrict__ p,
+                                        const double* __restrict__ ypart, int nsegMax,
+                                        const int* __restrict__ rowCell, const int* __restrict__ nseg,
+                                        const double* __restrict__ diag, double* x, double* rv, double* z,
+                                        double* part, double tol2, int maxit) {
+    if (all_done(st)) return;
+    bool act[kRhs];
+    double alpha[kRhs], rr[kRhs], rz[kRhs];
+#pragma unroll
+    for (int r = 0; r < kRhs; ++r) {
+        act[r] = !st[r].done;
+        alpha[r] = st[r].alpha;
+        rr[r] = rz[r] = 0.0;
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int ns = nseg[rowCell[i]];
+        const double di = diag ? diag[i] : 1.0;
+#pragma unroll
+        for (int r = 0; r < kRhs; ++r) {
+            if (!act[r]) continue;
+            double qi = 0.0;
+            for (int sg = 0; sg < ns; ++sg) qi += ypart[((int64_t)r * nsegMax + sg) * n + i];
+            const int64_t k = r * n + i;
+            x[k] += alpha[r] * p[k];
+            const double ri = rv[k] - alpha[r] * qi;
+            rv[k] = ri;
+            const double zi = diag ? ri / di : ri;
+            z[k] = zi;
+            rr[r] += ri * ri;
+            rz[r] += ri * zi;
+        }
+    }
+    for (int r = 0; r < kRhs; ++r) {
+        const double s1 = block_reduce(rr[r]);
+        const double s2 = block_reduce(rz[r]);
+        if (threadIdx.x == 0) {
+            part[(int64_t)(2 * r) * kVecBlocks + blockIdx.x] = s1;
+            part[(int64_t)(2 * r + 1) * kVecBlocks + blockIdx.x] = s2;
+        }
+    }
+    if (!draw_last_ticket(st)) return;
+    for (int r = 0; r < kRhs; ++r) {
+        if (!act[r]) continue;
+        double a = 0.0, b = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+            a += __ldcg(part + (int64_t)(2 * r) * kVecBlocks + i);
+            b += __ldcg(part + (int64_t)(2 * r + 1) * kVecBlocks + i);
+        }
+        const double rrs = block_reduce(a);
+        const double rzs = block_reduce(b);
+        if (threadIdx.x == 0) {
+            PcgState& S = st[r];
+            S.it += 1;
+            S.rr = rrs;
+            S.beta = rzs / S.rz;
+            S.rz = rzs;
+            if (rrs <= tol2 * S.bb) {
+                S.done = 1;
+            } else if (S.it >= maxit) {
+                S.status = ST_NOCONV;
+                S.done = 1;
+            }
+        }
+    }
+}
+
+__global__ void pcg_update_p_multi_kernel(int64_t n, const PcgState* st, const double* __restrict__ z, double* p) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int r = 0; r < kRhs; ++r)
+            if (!st[r].done) p[r * n + i] = z[r * n + i] + st[r].beta * p[r * n + i];
+}
+
+// x_r = 0, r_r = b_r, z_r = P^{-1} b_r, p_r = z_r; the scalars of every recurrence
+__global__ void pcg_init_multi_kernel(int64_t n, const double* __restrict__ b, const double* __restrict__ diag,
+                                      double* x, double* rv, double* z, double* p, double* part) {
+    double rz[kRhs], bb[kRhs];
+#pragma unroll
+    for (int r = 0; r < kRhs; ++r) rz[r] = bb[r] = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int r = 0; r < kRhs; ++r) {
+            const int64_t k = r * n + i;
+            const double bi = b[k];
+            const double zi = diag ? bi / diag[i] : bi;
+            x[k] = 0.0;
+            rv[k] = bi;
+            z[k] = zi;
+            p[k] = zi;
+            rz[r] += bi * zi;
+            bb[r] += bi * bi;
+        }
+    for (int r = 0; r < kRhs; ++r) {
+        const double s1 = block_reduce(rz[r]);
+        const double s2 = block_reduce(bb[r]);
+        if (threadIdx.x == 0) {
+            part[(int64_t)(2 * r) * kVecBlocks + blockIdx.x] = s1;
+            part[(int64_t)(2 * r + 1) * kVecBlocks + blockIdx.x] = s2;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) pcg_init_multi_scalars(const double* part, PcgState* st) {
+    for (int r = 0; r < kRhs; ++r) {
+        double a = 0.0, b = 0.0;
+        for (int i = threadIdx.x; i < kVecBlocks; i += blockDim.x) {
+            a += part[(int64_t)(2 * r) * kVecBlocks + i];
+            b += part[(int64_t)(2 * r + 1) * kVecBlocks + i];
+        }
+        const double rz = block_reduce(a);
+        const double bb = block_reduce(b);
+        if (threadIdx.x == 0) {
+            PcgState& S = st[r];
+            S.rz = rz;
+            S.bb = bb;
+            S.rr = bb;
+            S.it = 0;
+            S.ticket = 0;
+            S.status = ST_OK;
+            S.done = bb == 0.0 ? 1 : 0;
+        }
+    }
+}
+
+size_t pcg_multi_work_doubles(const mlb_ctx* ctx) {
+    const int64_t n = ctx->nwav;
+    return (size_t)kRhs * (5 * n + (int64_t)ctx->pan.nsegMax * n) + (size_t)kRhs * ctx->pan.nwork +
+           (size_t)2 * kRhs * kVecBlocks + kRhs * (sizeof(PcgState) / sizeof(double) + 1);
+}
+
+// kRhs PCG solves C~_W x_r = b_r (b, x: kRhs x nwav, device) on the FP32
+// panels of the mixed path; work: pcg_multi_work_doubles(ctx) doubles (device).
+// iters (host, kRhs) receives each recurrence's iteration count.
+mlb_status pcg_run_multi(mlb_ctx* ctx, const double* b, double* x, double* work, int* iters) {
+    if (!ctx->pan.vals32 || ctx->opts.matrix_free || ctx->pan.nwork == 0)
+        return fail(ctx, MLB_EINVAL, "several right-hand sides need the assembled FP32 panels");
+    cudaStream_t st = ctx->stream;
+    const int64_t n = ctx->nwav;
+    double* rv = work;
+    double* z = rv + kRhs * n;
+    double* p = z + kRhs * n;
+    double* ypart = p + kRhs * n;
+    double* part = ypart + (int64_t)kRhs * ctx->pan.nsegMax * n;
+    double* part2 = part + (int64_t)kRhs * ctx->pan.nwork;
+    PcgState* S = reinterpret_cast<PcgState*>(part2 + 2 * kRhs * kVecBlocks);
+    const double* diag = ctx->opts.precond ? ctx->diag : nullptr;
+    const double tol2 = ctx->opts.pcg_rtol * ctx->opts.pcg_rtol;
+    pcg_init_multi_kernel<<<kVecBlocks, 256, 0, st>>>(n, b, diag, x, rv, z, p, part2);
+    pcg_init_multi_scalars<<<1, 256, 0, st>>>(part2, S);
+    MLB_CHECK_LAUNCH(ctx, "pcg_init_multi");
+    ctx->launches += 1;
+    struct Owned {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        ~Owned() {
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+        }
+    } own;
+    constexpr int chunk = 8;
+    MLB_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < chunk; ++i) {
+        spmm_panel_f32_kernel<<<ctx->pan.nwork, 256, 0, st>>>(ctx->pan, ctx->pan.vals32, ctx->cells.k,
+                                                             ctx->cells.wOff, p, n, ypart, part, S);
+        pcg_update_multi_kernel<<<kVecBlocks, 256, 0, st>>>(n, S, p, ypart, ctx->pan.nsegMax, ctx->pan.rowCell,
+                                                            ctx->pan.nseg, diag, x, rv, z, part2, tol2,
+                                                            ctx->opts.pcg_maxit);
+        pcg_update_p_multi_kernel<<<kVecBlocks, 256, 0, st>>>(n, S, z, p);
+    }
+    MLB_CUDA(ctx, cudaStreamEndCapture(st, &own.graph));
+    MLB_CUDA(ctx, cudaGraphInstantiate(&own.exec, own.graph, 0));
+    PcgState hs[kRhs];
+    for (;;) {
+        MLB_CUDA(ctx, cudaGraphLaunch(own.exec, st));
+        ctx->launches += 3 * chunk;
+        MLB_CUDA(ctx, cudaMemcpyAsync(hs, S, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        MLB_CUDA(ctx, cudaStreamSynchronize(st));
+        bool done = true;
+        for (int r = 0; r < kRhs; ++r) done = done && hs[r].done;
+        if (done) break;
+    }
+    for (int r = 0; r < kRhs; ++r) {
+        if (iters) iters[r] = hs[r].it;
+        if (hs[r].status == ST_BREAKDOWN) return fail(ctx, MLB_EBREAKDOWN, "PCG breakdown: p^T C~_W p <= 0");
+        if (hs[r].status == ST_NOCONV) return fail(ctx, MLB_ENOCONV, "PCG did not reach pcg_rtol within pcg_maxit");
+    }
+    return MLB_OK;
+}
+
 }  // namespace mlb
