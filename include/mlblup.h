@@ -11,6 +11,9 @@
  *   solve       C~_W gamma_W = W Z by diagonal PCG, gamma = W^T gamma_W,
  *               beta = (X^T X)^{-1} X^T (Z - C gamma)            (Sec. 5.2, eqs. Spatial:eqn1-3; Sec. 6.2)
  *   predict     Z(x0) = k(x0)^T beta + c(x0)^T gamma            (Sec. 5.2, eq. Spatial)
+ *   also        the gradient of a held-out loss in log(rho), log(nugget) (adjoint),
+ *               the kriging MSE at targets (formula after eq. Spatial), the
+ *               multilevel log-likelihood (Sec. 5.1) and many problems per call.
  *
  * Conventions (all entry points):
  *  - Every call returns an mlb_status; no exception crosses the ABI.  On error
@@ -23,7 +26,8 @@
  *    the context's stream (_dev variants, which take device pointers and do
  *    not synchronise).  The context owns all device memory it allocates.
  *  - Call order: mlb_build_basis -> mlb_assemble -> mlb_solve -> mlb_predict
- *    or mlb_grad.  A call made before its prerequisite returns MLB_ESTATE.
+ *    or mlb_grad (mlb_mse and mlb_loglik need only mlb_assemble).  A call
+ *    made before its prerequisite returns MLB_ESTATE.
  *    A new mlb_build_basis invalidates the assembly and the solution; a new
  *    mlb_assemble invalidates the solution.
  *  - Matern smoothness nu must be 0.5, 1.5 or 2.5 (closed forms of the
