@@ -76,3 +76,57 @@ def test_missing_trend_adjoint_is_caught(monkeypatch):
     monkeypatch.setattr(grad.np.linalg, "solve", zero_lambda0)
     m = grad.grad_multilevel(P.points, P.Z, P.targets, P.y_targets, 1, 1.5, 0.3, 1e-4, 12)
     assert not np.allclose(m[1:], d[1:], rtol=1e-4)
+
+
+def test_mse_without_the_trend_correction_is_caught():
+    """Planted: MSE = 1 - c^T C^{-1} c (simple-kriging variance, the u^T A^{-1} u
+    term of the unknown trend dropped).  The one-observation closed form
+    2 - 2 phi(r) fails."""
+    x1 = np.array([[0.3, 0.7]])
+    tg = np.array([[0.5, 0.5], [0.9, 0.1]])
+    C = matern.covariance(x1, 1.5, 0.4, 0.0)
+    c0 = matern.kernel_matrix(x1, tg, 1.5, 0.4)
+    bad = 1.0 - np.einsum("ik,ik->k", c0, np.linalg.solve(C, c0))
+    r = np.linalg.norm(tg - x1, axis=1)
+    assert not np.allclose(bad, 2.0 - 2.0 * matern.matern(r, 1.5, 0.4), rtol=1e-6)
+
+
+def test_slq_without_the_probe_norm_is_caught(monkeypatch):
+    """Planted: the stochastic Lanczos estimate forgets the |v|^2 factor of
+    each probe.  The unit-probe exactness pin fails as soon as the probes are
+    not unit vectors, and the Hutchinson bound fails for Rademacher probes."""
+    from oracle import loglik
+    rng = np.random.default_rng(4)
+    Q, _ = np.linalg.qr(rng.standard_normal((60, 60)))
+    A = Q @ np.diag(np.logspace(0.5, 1.5, 60)) @ Q.T
+    probes = rng.choice([-1.0, 1.0], size=(200, 60))
+
+    def bad(A, probes, k):
+        tot = 0.0
+        for v in probes:
+            a, b = loglik.lanczos_tridiagonal(A, v, k)
+            th, U = np.linalg.eigh(np.diag(a) + np.diag(b, 1) + np.diag(b, -1))
+            tot += float(np.sum(U[0] ** 2 * np.log(th)))
+        return tot / len(probes)
+
+    exact = np.linalg.slogdet(A)[1]
+    lam, U = np.linalg.eigh(A)
+    L = (U * np.log(lam)) @ U.T
+    sd = math.sqrt(2.0 * (np.sum(L ** 2) - np.sum(np.diag(L) ** 2)) / probes.shape[0])
+    assert abs(loglik.slq_logdet(A, probes, 20) - exact) < 4.0 * sd
+    assert abs(bad(A, probes, 20) - exact) > 4.0 * sd
+
+
+def test_loglik_with_the_dense_covariance_is_caught():
+    """Planted: the quadratic form taken with C instead of C_W
+    (Z^T C^{-1} Z).  The REML quadratic-form pin fails."""
+    P = wl.small_problem(31, 140, 2, 1, nu=1.5, rho=0.3, nugget=1e-3, leaf_size=12)
+    C = matern.covariance(P.points, P.nu, P.rho, P.nugget)
+    from oracle import design as od
+    lo, hi = od.box(P.points)
+    X = od.design_matrix(P.points, P.w, lo, hi)
+    Ci_Z = np.linalg.solve(C, P.Z)
+    Ci_X = np.linalg.solve(C, X)
+    q_reml = P.Z @ Ci_Z - (X.T @ Ci_Z) @ np.linalg.solve(X.T @ Ci_X, X.T @ Ci_Z)
+    bad = float(P.Z @ Ci_Z)
+    assert abs(bad - q_reml) > 1e-6 * abs(q_reml)
