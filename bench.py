@@ -8,8 +8,9 @@ trend step and the prediction at the targets (every row of the hot path).
 Workload (default): n = 32,768 points uniform in [0,1]^5, Matern nu = 3/2,
 rho = 0.3, nugget 1e-4, w = 1 (p = 6), leaf size 64, tau = inf (the full
 C_W, 1.07e9 entries), PCG tol 1e-10, 4,096 held-out targets.  Synthetic,
-seeded.  `--workload config2` (n = 65,536 in [0,1]^3 with 8 tight clusters,
-nugget 1e-6, tau = 2 diameters) and `config3` are available too.
+seeded.  `--workload clustered_3d` (n = 65,536 in [0,1]^3 with 8 tight
+clusters, nugget 1e-6, tau = 2 diameters), `uniform_10d` (d = 10,
+matrix-free) and `batched_problems` are available too.
 
 Prints one JSON line.  `--impl reference` times the CPU oracle instead.
 """
@@ -45,9 +46,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--single", action="store_true", help="measure only --precision")
-    ap.add_argument("--workload", default="config5", choices=["config5", "config2", "config3", "config4"])
+    ap.add_argument("--workload", default="heldout_5d",
+                    choices=["heldout_5d", "clustered_3d", "uniform_10d", "batched_problems"])
     ap.add_argument("--count", type=int, default=64,
-                    help="config4: number of problems (the full workload is 512; 64 keeps both precisions "
+                    help="batched_problems: number of problems (the full workload is 512; 64 keeps both precisions "
                          "with 3 + 3 steps within minutes)")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--targets", type=int, default=None)
@@ -158,7 +160,9 @@ def workload(args, rank=0):
         kw["N"] = args.n
     if args.targets:
         kw["M"] = args.targets
-    return getattr(wl, args.workload)(**kw)
+    P = getattr(wl, args.workload)(**kw)
+    P.meta["generator"] = args.workload     # lets the oracle sample draw the same workload
+    return P
 
 
 def matrix_free(P) -> bool:
@@ -198,7 +202,7 @@ def cpu_baseline(P, sample_n=2048, sample_m=512):
     kernel evaluation."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import bench, sys; print(bench._oracle_sample(%r, %d, %d, %d, %d))"
-            % (P.name.split("_")[0], sample_n, sample_m, P.N, P.targets.shape[0]))
+            % (P.meta["generator"], sample_n, sample_m, P.N, P.targets.shape[0]))
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
@@ -372,7 +376,7 @@ def run_batched(args, rank, world, local_rank):
     from paper_1701_00285_gb300.binding import batch_last_launches, batch_last_phase_ms, batch_solve
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    every = wl.config4(count=args.count * world)
+    every = wl.batched_problems(count=args.count * world)
     probs = [every[i] for i in shard_indices(args.count, rank, world)]
     items = [{"points": q.points, "w": q.w, "nu": q.nu, "rho": q.rho, "nugget": q.nugget,
               "tau_factor": q.tau_factor, "Z": q.Z, "targets": q.targets} for q in probs]
@@ -402,7 +406,7 @@ def run_batched(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": "BLUP solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * out["mixed"]["s"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-            "config": {"workload": f"config4: {args.count} independent problems per GPU, n log-uniform [500, 8000], "
+            "config": {"workload": f"batched_problems: {args.count} independent problems per GPU, n log-uniform [500, 8000], "
                                    f"d in {{2,3,5}}, nu in {{1/2,3/2,5/2}}, rho ~ U[0.1,0.5], w=1, leaf 64, "
                                    f"tau=inf, nugget 1e-4, PCG tol 1e-10, 1024 targets each",
                        "precision": "mixed", "parallelism": f"problem-sharded{world}",
@@ -546,7 +550,7 @@ def main():
         dist.init_process_group(backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.workload == "config4":
+    elif args.workload == "batched_problems":
         run_batched(args, rank, world, local_rank)
     elif args.mse:
         run_mse(args, rank, world, local_rank)

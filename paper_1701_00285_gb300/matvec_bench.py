@@ -33,7 +33,7 @@ def main(argv=None) -> None:
     import workloads as wl
     from .binding import Context
 
-    P = wl.config3(N=a.n, M=512) if a.matrix_free else wl.config5(N=a.n, M=512)
+    P = wl.uniform_10d(N=a.n, M=512) if a.matrix_free else wl.heldout_5d(N=a.n, M=512)
     leaf = a.leaf_size or P.leaf_size
     st = torch.cuda.Stream()
     for prec in a.precision.split(","):

@@ -31,7 +31,7 @@ def pkg():
 
 @pytest.fixture(scope="module")
 def problem():
-    return wl.config5()
+    return wl.heldout_5d()
 
 
 # residual tolerance: the PCG stops at 1e-10 on the W-system; the mixed path

@@ -277,7 +277,7 @@ def test_grad_matches_dense_oracle_gradient(pkg):
     """n = 2,000 subsample of the differentiation workload, FP64 path vs the
     oracle's dense adjoint gradient."""
     from oracle import grad as og
-    P = wl.subsample(wl.config5(N=8192, M=1024), 2000, seed=3, m=300)
+    P = wl.subsample(wl.heldout_5d(N=8192, M=1024), 2000, seed=3, m=300)
     ctx = ctx_for(pkg, P, rtol=1e-12, pcg_maxit=50000)
     ctx.assemble(P.nu, P.rho, P.nugget, math.inf)
     ctx.solve(P.Z)
@@ -346,7 +346,7 @@ def test_high_dimension_subsample_matrix_free(pkg):
     """2,048-point subsample of the d = 10 workload (nu = 5/2, rho = 0.5,
     nugget 1e-5, w = 2, leaf 128): FP64 and mixed three-step PCG vs the dense
     oracle."""
-    P = wl.subsample(wl.config3(N=16384, M=512), 2048, seed=2, m=256)
+    P = wl.subsample(wl.uniform_10d(N=16384, M=512), 2048, seed=2, m=256)
     ref = dense.dense_blup(P.points, P.Z, P.targets, P.w, P.nu, P.rho, P.nugget)
     got = {}
     for prec in ("fp64", "mixed"):
@@ -364,7 +364,7 @@ def test_batched_problems_mixed_vs_oracle(pkg):
     three nu, rho in [0.1, 0.5]) truncated at tau = 2 diameters, both
     precisions vs the multilevel oracle's exact solve of the same truncated
     system."""
-    probs = [dataclasses.replace(q, tau_factor=2.0) for q in wl.config4(count=60) if q.N <= 1400][:4]
+    probs = [dataclasses.replace(q, tau_factor=2.0) for q in wl.batched_problems(count=60) if q.N <= 1400][:4]
     assert len(probs) == 4
     for P in probs:
         B = mlblup.setup(P.points, P.w, P.leaf_size)
@@ -400,7 +400,7 @@ def test_batch_solve_matches_oracle(pkg, prec, tol):
     tau = 2 diameters) through mlb_batch_solve, each against the multilevel
     oracle's exact solve of its own truncated system."""
     from paper_1701_00285_gb300.binding import batch_solve
-    probs = [dataclasses.replace(q, tau_factor=2.0) for q in wl.config4(count=80) if q.N <= 1500][:6]
+    probs = [dataclasses.replace(q, tau_factor=2.0) for q in wl.batched_problems(count=80) if q.N <= 1500][:6]
     items = [{"points": q.points, "w": q.w, "nu": q.nu, "rho": q.rho, "nugget": q.nugget,
               "tau_factor": q.tau_factor, "Z": q.Z, "targets": q.targets[:150]} for q in probs]
     res, ms, st = batch_solve(items, precision=prec, pcg_rtol=1e-12, pcg_maxit=50000)
@@ -422,7 +422,7 @@ def test_batch_solve_mixed_sizes_dense_oracle(pkg, prec, tol):
     full-grid PCG on the stream pool.  tau = infinity, so each must equal the
     dense BLUP of its own data."""
     from paper_1701_00285_gb300.binding import batch_solve
-    small = [q for q in wl.config4(count=40) if q.N <= 1000][:2]
+    small = [q for q in wl.batched_problems(count=40) if q.N <= 1000][:2]
     big = wl.small_problem(590, 2600, 3, 1, nu=1.5, rho=0.3, nugget=1e-4, leaf_size=64, M=150)
     probs = small + [big]
     items = [{"points": q.points, "w": q.w, "nu": q.nu, "rho": q.rho, "nugget": q.nugget,

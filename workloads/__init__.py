@@ -31,8 +31,8 @@ import numpy as np
 BASE_SEED = 170100285
 
 __all__ = [
-    "BASE_SEED", "Problem", "config1", "config2", "config3", "config4",
-    "config5", "small_problem", "subsample",
+    "BASE_SEED", "Problem", "dense_2d", "clustered_3d", "uniform_10d", "batched_problems",
+    "heldout_5d", "small_problem", "subsample",
 ]
 
 
@@ -108,7 +108,7 @@ def _mixture(rng, n, d, centres, sigma):
     return centres[lab] + sigma * rng.standard_normal((n, d))
 
 
-def config1() -> Problem:
+def dense_2d() -> Problem:
     """Dense BLUP check: 1,000 uniform points in [0,1]^2, exponential kernel."""
     r_pts, r_beta, r_tgt = _streams(1, 3)
     N, d, w = 1000, 2, 1
@@ -116,12 +116,12 @@ def config1() -> Problem:
     coef = r_beta.standard_normal(math.comb(d + w, w))
     z = _trend(x, w, coef) + np.sin(4 * np.pi * x[:, 0]) * np.cos(2 * np.pi * x[:, 1])
     tg = r_tgt.uniform(0.0, 1.0, size=(200, d))
-    return Problem("config1_dense_n1000_d2", x, z, tg, nu=0.5, rho=0.25, nugget=0.0,
+    return Problem("dense_2d_n1000", x, z, tg, nu=0.5, rho=0.25, nugget=0.0,
                    w=w, leaf_size=64, tau_factor=math.inf, pcg_rtol=1e-12,
                    meta={"trend_coef": coef})
 
 
-def config2(N: int = 65536, M: int = 16384) -> Problem:
+def clustered_3d(N: int = 65536, M: int = 16384) -> Problem:
     """Multilevel FP64: half uniform, half 8-centre Gaussian mixture in [0,1]^3."""
     r_pts, r_mix, r_beta, r_om, r_noise, r_tgt = _streams(2, 6)
     d, w = 3, 2
@@ -136,12 +136,12 @@ def config2(N: int = 65536, M: int = 16384) -> Problem:
     mt = M // 2
     tg = np.concatenate([r_tgt.uniform(0.0, 1.0, size=(mt, d)),
                          _mixture(r_tgt, M - mt, d, centres, 0.03)])
-    return Problem(f"config2_ml_n{N}_d3", x, z, tg, nu=1.5, rho=0.2, nugget=1e-6,
+    return Problem(f"clustered_3d_n{N}", x, z, tg, nu=1.5, rho=0.2, nugget=1e-6,
                    w=w, leaf_size=64, tau_factor=2.0, pcg_rtol=1e-10,
                    meta={"trend_coef": coef, "omega": omega})
 
 
-def config3(N: int = 262144, M: int = 65536) -> Problem:
+def uniform_10d(N: int = 262144, M: int = 65536) -> Problem:
     """Mixed precision, high dimension: uniform points in [0,1]^10."""
     r_pts, r_beta, r_om, r_noise, r_tgt = _streams(3, 5)
     d, w = 10, 2
@@ -151,12 +151,12 @@ def config3(N: int = 262144, M: int = 65536) -> Problem:
     noise = math.sqrt(1e-4) * r_noise.standard_normal(N)
     z = _observe(x, w, coef, omega, noise)
     tg = r_tgt.uniform(0.0, 1.0, size=(M, d))
-    return Problem(f"config3_mf_n{N}_d10", x, z, tg, nu=2.5, rho=0.5, nugget=1e-5,
+    return Problem(f"uniform_10d_n{N}", x, z, tg, nu=2.5, rho=0.5, nugget=1e-5,
                    w=w, leaf_size=128, tau_factor=math.inf, pcg_rtol=1e-8,
                    meta={"trend_coef": coef, "omega": omega})
 
 
-def config4(count: int = 512, M: int = 1024, n_lo: int = 500, n_hi: int = 8000) -> list[Problem]:
+def batched_problems(count: int = 512, M: int = 1024, n_lo: int = 500, n_hi: int = 8000) -> list[Problem]:
     """Batched: independent problems with log-uniform sizes, mixed d, nu, rho.
 
     tau = infinity (the exact BLUP of every problem): with tau = 2 level-mean
@@ -177,13 +177,13 @@ def config4(count: int = 512, M: int = 1024, n_lo: int = 500, n_hi: int = 8000) 
         noise = 1e-2 * r_noise.standard_normal(n)
         z = _observe(x, w, coef, omega, noise)
         tg = r_tgt.uniform(0.0, 1.0, size=(M, d))
-        probs.append(Problem(f"config4_batch{i}_n{n}_d{d}", x, z, tg, nu=nu, rho=rho,
+        probs.append(Problem(f"batch{i}_n{n}_d{d}", x, z, tg, nu=nu, rho=rho,
                              nugget=1e-4, w=w, leaf_size=64, tau_factor=math.inf,
                              pcg_rtol=1e-10, meta={"trend_coef": coef}))
     return probs
 
 
-def config5(N: int = 32768, M: int = 4096) -> Problem:
+def heldout_5d(N: int = 32768, M: int = 4096) -> Problem:
     """Differentiation: uniform points in [0,1]^5 with held-out observations."""
     r_pts, r_beta, r_om, r_noise, r_tgt, r_tnoise = _streams(5, 6)
     d, w = 5, 1
@@ -193,7 +193,7 @@ def config5(N: int = 32768, M: int = 4096) -> Problem:
     z = _observe(x, w, coef, omega, math.sqrt(1e-4) * r_noise.standard_normal(N))
     tg = r_tgt.uniform(0.0, 1.0, size=(M, d))
     yt = _observe(tg, w, coef, omega, math.sqrt(1e-4) * r_tnoise.standard_normal(M))
-    return Problem(f"config5_grad_n{N}_d5", x, z, tg, nu=1.5, rho=0.3, nugget=1e-4,
+    return Problem(f"heldout_5d_n{N}", x, z, tg, nu=1.5, rho=0.3, nugget=1e-4,
                    w=w, leaf_size=64, tau_factor=math.inf, pcg_rtol=1e-10,
                    y_targets=yt, meta={"trend_coef": coef, "omega": omega})
 
