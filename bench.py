@@ -329,9 +329,10 @@ def measure(pkg, torch, P, precision, args, dev, local_rank, world, stream):
     return out
 
 
-def e2e_run(ctx, P, args, world, torch):
+def e2e_run(ctx, P, args, world, torch, dev=None):
     hp, hz, ht = P.points.copy(), P.Z.copy(), P.targets.copy()
     ctx.set_stream(None)
+    barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -340,7 +341,7 @@ def e2e_run(ctx, P, args, world, torch):
         hb, _ = ctx.solve(hz)
         hy = ctx.predict(ht)
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    dt = max_over_ranks(time.perf_counter() - t0, world, dev)
     return {"value": world * args.steps / dt, "unit": "BLUP solves/s",
             "h2d_bytes_per_step": int(hp.nbytes + hz.nbytes + ht.nbytes),
             "d2h_bytes_per_step": int(hy.nbytes + hb.nbytes)}
@@ -472,7 +473,7 @@ def run_ours(args, rank, world, local_rank):
     head = measure(pkg, torch, P, args.precision, args, dev, local_rank, world, stream)
     other_prec = "fp64" if args.precision == "mixed" else "mixed"
     other = None if args.single else measure(pkg, torch, P, other_prec, args, dev, local_rank, world, stream)
-    e2e = None if args.no_e2e else e2e_run(head["ctx"], P, args, world, torch)
+    e2e = None if args.no_e2e else e2e_run(head["ctx"], P, args, world, torch, dev)
     info = head["info"]
     if head["matrix_free"]:
         # three-step product: the N x N FP32 kernel sum dominates; FP32 pipes
