@@ -25,6 +25,10 @@ What it computes, in the paper's order and notation:
                   log(nugget) by the adjoint of the saddle-point system (the
                   paper has no gradient; this is the plain adjoint of its
                   BLUP equations).
+* ``loglik``   -- the multilevel log-likelihood of the full transform (Sec.
+                  5.1) and a stochastic Lanczos quadrature estimate of its
+                  log-determinant; the kriging MSE is ``dense.mse_at`` (the
+                  formula after eq. Spatial).
 
 Readings of points where the paper is silent or garbled are stated in each
 function's docstring.
