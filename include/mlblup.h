@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define MLB_ABI_VERSION 1
+#define MLB_ABI_VERSION 2
 
 typedef struct mlb_ctx mlb_ctx;
 
@@ -96,6 +96,10 @@ typedef struct {
     int64_t nnz_unique;        /* entries of the blocks j >= i (each symmetric pair once) */
     int64_t launches;          /* kernels this context has launched since mlb_create */
     int64_t col_total;         /* column indices stored (one list per row panel) */
+    int64_t product_values;    /* matrix values one product C~_W u streams (FP32 on the
+                                  mixed path, FP64 otherwise; 0 when matrix-free) */
+    int symmetric;             /* 1: the product streams each symmetric pair of entries once
+                                  (mixed path, every cell pair admissible); 0: both triangles */
 } mlb_info;
 
 /* Fills *opts with defaults: FP64, n0 = 64, rtol 1e-10, maxit 20000, diagonal
@@ -251,6 +255,12 @@ mlb_status mlb_cw_matvec_dev(mlb_ctx* ctx, const double* u_dev, double* out_dev)
  * the context's stream without synchronising.  All calls on one device share
  * the array: calls whose kernels overlap in time race. */
 mlb_status mlb_apply_W_noalloc(mlb_ctx* ctx, const double* v_dev, double* out_dev);
+
+/* Figures of the current assembly (nnz, nnz_unique, blocks, col_total,
+ * product_values, symmetric, ms_assemble) and of the last solve (iterations,
+ * converged, rel_residual, ms_pcg, ms_beta; zero before one), plus launches.
+ * info: host.  MLB_ESTATE before mlb_assemble. */
+mlb_status mlb_get_info(const mlb_ctx* ctx, mlb_info* info);
 
 /* Number of kernels the context has launched since mlb_create. */
 mlb_status mlb_get_launch_count(const mlb_ctx* ctx, int64_t* count);

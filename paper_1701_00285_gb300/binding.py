@@ -42,7 +42,8 @@ class Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("nnz", ctypes.c_int64), ("blocks", ctypes.c_int64), ("ms_assemble", ctypes.c_double),
                 ("ms_pcg", ctypes.c_double), ("ms_beta", ctypes.c_double),
-                ("nnz_unique", ctypes.c_int64), ("launches", ctypes.c_int64), ("col_total", ctypes.c_int64)]
+                ("nnz_unique", ctypes.c_int64), ("launches", ctypes.c_int64), ("col_total", ctypes.c_int64),
+                ("product_values", ctypes.c_int64), ("symmetric", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -91,6 +92,7 @@ _SIGS = {
     "mlb_cw_matvec": (ctypes.c_int, [_P, _P, _P]),
     "mlb_cw_matvec_dev": (ctypes.c_int, [_P, _P, _P]),
     "mlb_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "mlb_get_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
     "mlb_apply_W_noalloc": (ctypes.c_int, [_P, _P, _P]),
     "mlb_get_pattern": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "mlb_kernel_sum": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
@@ -330,6 +332,12 @@ class Context:
     def apply_W_noalloc(self, v_ptr: int, out_ptr: int):
         """W v on caller-owned device buffers, with no device allocation."""
         self._check(lib().mlb_apply_W_noalloc(self._h, v_ptr, out_ptr))
+
+    def info(self) -> dict:
+        """Figures of the current assembly and of the last solve (mlb_get_info)."""
+        info = Info()
+        self._check(lib().mlb_get_info(self._h, ctypes.byref(info)))
+        return info.as_dict()
 
     def launch_count(self) -> int:
         c = _I64()

@@ -754,7 +754,19 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
     dfree(A, X0);
     dfree(A, X1);
     if (mixed) {
-        // the mixed path keeps C~_W in FP32: half the bytes per product.  Its
+        // complete pattern: each symmetric pair stored once in FP32 (symv.cu)
+        bool complete = ctx->allow_sym && ctx->nwav > 0;
+        for (int g = 0; g < ncell && complete; ++g)
+            if (ctx->hcells[g].k > 0 && hn[g] != ctx->nwav) complete = false;
+        if (complete) {
+            mlb_status ss = build_sym(ctx);
+            if (ss != MLB_OK) return ss;
+            dfree(A, pan.vals);
+            pan.vals = nullptr;
+            return MLB_OK;
+        }
+        // otherwise the mixed path keeps the row panels in FP32: half the
+        // bytes of the FP64 panels per product.  Its
         // product runs one CTA per kItemRows rows x kSegCols columns of a
         // panel, heaviest items first, so the last wave of CTAs is short.
         std::vector<std::pair<int64_t, int4>> items;

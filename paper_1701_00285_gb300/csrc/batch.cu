@@ -211,6 +211,8 @@ mlb_status setup_one(Job& j, const mlb_opts& o, cudaStream_t st) {
     mlb_set_stream(j.ctx, st);
     s = mlb_build_basis(j.ctx, P.points, P.n, P.d, P.w);
     if (s != MLB_OK) return s;
+    // the persistent launch reads the row panels of the systems it solves
+    j.ctx->allow_sym = j.ctx->nwav > kCtaRows;
     s = mlb_assemble(j.ctx, &P.theta, P.tau_factor);
     if (s != MLB_OK) return s;
     mlb_ctx* c = j.ctx;

@@ -487,6 +487,7 @@ mlb_status mlb_assemble(mlb_ctx* ctx, const mlb_theta* th, double tau_factor) {
         int* rc = ctx->pan.rowCell;
         ctx->pan = Panels{};
         ctx->pan.rowCell = rc;
+        ctx->sym = SymPanels{};
         ctx->diag = nullptr;
     }
     ctx->theta = *th;
@@ -649,6 +650,23 @@ mlb_status mlb_cw_matvec_dev(mlb_ctx* ctx, const double* u_dev, double* out_dev)
     if (ctx->state < 2) return fail(ctx, MLB_ESTATE, "no assembly");
     cudaSetDevice(ctx->opts.device);
     return cw_matvec_dev(ctx, u_dev, out_dev);
+}
+
+mlb_status mlb_get_info(const mlb_ctx* ctx, mlb_info* info) {
+    if (!ctx || !info) return MLB_EINVAL;
+    if (ctx->state < 2) return MLB_ESTATE;
+    mlb_info I{};
+    if (ctx->state >= 3) I = ctx->last_info;
+    I.nnz = ctx->pan.nnz;
+    I.nnz_unique = ctx->pan.nnzUnique;
+    I.blocks = ctx->pan.blocks;
+    I.col_total = ctx->sym.vals ? 0 : ctx->pan.colTotal;
+    I.symmetric = ctx->sym.vals ? 1 : 0;
+    I.product_values = ctx->opts.matrix_free ? 0 : (ctx->sym.vals ? ctx->sym.stored : ctx->pan.stored);
+    I.ms_assemble = ctx->ms_assemble;
+    I.launches = ctx->launches;
+    *info = I;
+    return MLB_OK;
 }
 
 mlb_status mlb_get_launch_count(const mlb_ctx* ctx, int64_t* count) {

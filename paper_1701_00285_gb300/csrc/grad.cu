@@ -261,7 +261,7 @@ mlb_status mse_dev(mlb_ctx* ctx, const double* tg, int64_t M, double* out) {
     const int p = ctx->p, d = ctx->d;
     // on the FP32 panels kRhs targets share each pass over C~_W (one PCG
     // recurrence per target, one product for all); otherwise one at a time
-    const bool multi = ctx->pan.vals32 && !ctx->opts.matrix_free && ctx->pan.nwork > 0;
+    const bool multi = !ctx->opts.matrix_free && (ctx->sym.vals || (ctx->pan.vals32 && ctx->pan.nwork > 0));
     const int R = multi ? kRhs : 1;
     Arena tmp;
     double* A = (double*)dalloc(ctx, tmp, sizeof(double) * R * N);      // c(x0) per slot

@@ -75,6 +75,40 @@ inline size_t max_work_items(int ncell, int64_t N) {
     return ((size_t)ncell + (size_t)(N / kItemRows) + 1) * (size_t)((N + kSegCols - 1) / kSegCols);
 }
 
+// Symmetric packed storage of a complete C~_W in FP32 (mixed path, every
+// cell pair admissible): each symmetric pair of entries is stored once.  The
+// wavelet rows are grouped in blocks of kSymRows; block b keeps its rows from
+// its own first column (b kSymRows) to the last, i.e. its diagonal square in
+// full and everything to the right of it, row-major with the row stride
+// sym_width(nwav, b) (a multiple of 4, zero padded).  The product streams
+// every stored value once and applies it twice (B x to the block's rows and
+// B^T x to the columns' rows).  Work items are (block, segment of kSymSeg
+// columns), heaviest first; an item's row sums go to rowpart (by segment) and
+// its column sums to colpart (by block), both summed in a fixed order by the
+// consumer, so the product is deterministic.
+constexpr int kSymRows = 128;
+constexpr int kSymSeg = 2048;
+
+__host__ __device__ inline int64_t sym_width(int64_t nwav, int b) {
+    return ((nwav - (int64_t)b * kSymRows) + 3) & ~(int64_t)3;
+}
+__host__ __device__ inline int sym_nseg(int64_t nwav, int b) {
+    return (int)((sym_width(nwav, b) + kSymSeg - 1) / kSymSeg);
+}
+
+struct SymPanels {
+    int nblk = 0;               // row blocks
+    int64_t stored = 0;         // FP32 values stored
+    float* vals = nullptr;
+    int64_t* off = nullptr;     // per block: offset of its first value
+    int2* work = nullptr;       // (block, segment), heaviest first
+    int nwork = 0;
+    int nsegMax = 0;
+    int nrhs = 0;               // right-hand sides the partial buffers hold
+    double* rowpart = nullptr;  // nrhs x nsegMax x nwav
+    double* colpart = nullptr;  // nrhs x nblk x nwav
+};
+
 struct PcgState {
     double rz, rr, bb, alpha, beta, pq;
     int it, done, status;
@@ -128,6 +162,8 @@ struct mlb_ctx {
     mlb_theta theta{};
     double tau_factor = 0;
     mlb::Panels pan;
+    mlb::SymPanels sym;            // mixed path, complete pattern: each symmetric pair stored once
+    bool allow_sym = true;         // false: keep the FP32 row panels instead (batched small systems)
     double* diag = nullptr;        // diag(C~_W)
     double ms_assemble = 0;
     mlb::Arena arena_asm;
@@ -179,6 +215,16 @@ mlb_status gather_kd(mlb_ctx* ctx, const double* v_user, double* v_kd);   // cal
 mlb_status scatter_kd(mlb_ctx* ctx, const double* v_kd, double* v_user);  // kd -> caller order
 // assemble.cu
 mlb_status assemble_dev(mlb_ctx* ctx);
+// symv.cu: the symmetric packed FP32 storage (from the FP64 panels of a
+// complete pattern) and its product
+mlb_status build_sym(mlb_ctx* ctx);
+// partial buffers for nrhs simultaneous products (grown on demand)
+mlb_status sym_reserve(mlb_ctx* ctx, int nrhs);
+// products of the nrhs vectors x (nrhs x nwav) into the partial buffers; part
+// (nrhs x nwork) and st (nrhs states) may be nullptr outside the PCG
+void sym_launch(mlb_ctx* ctx, const double* x, int nrhs, double* part, PcgState* st);
+// out = the sums of the partials of right-hand side 0
+void sym_reduce(mlb_ctx* ctx, double* out);
 // solve.cu
 mlb_status cw_matvec_dev(mlb_ctx* ctx, const double* u, double* out);
 mlb_status solve_dev(mlb_ctx* ctx, const double* Z_kd, mlb_info* info);

@@ -19,60 +19,11 @@
 
 #include "internal.h"
 #include "matern.cuh"
+#include "pcg_device.cuh"
 
 namespace mlb {
 
-constexpr int kVecBlocks = 512;
 constexpr int64_t kFusePMax = 16384;   // longest vector whose p update the last CTA does
-
-enum { ST_OK = 0, ST_BREAKDOWN = 1, ST_NOCONV = 2 };
-
-__device__ double block_reduce(double v) {
-    __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int i = 0; i < nw; ++i) s += red[i];
-    }
-    __syncthreads();
-    return s;   // valid in thread 0
-}
-
-// Last-CTA reduction: every CTA of a launch has written its partial sums;
-// each then draws a ticket, and the CTA that draws the last one (after a
-// fence, so it sees every partial) finishes the reduction in a fixed order.
-// No CTA waits for another.  The ticket is reset for the next launch.
-__device__ bool draw_last_ticket(PcgState* st) {
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
-        if (last) st->ticket = 0;
-    }
-    __syncthreads();
-    if (last) __threadfence();
-    return last;
-}
-
-// alpha = (r.z) / (p.q) from the per-CTA partials of p.q
-__device__ void pcg_alpha_finish(const double* part, int nparts, PcgState* st) {
-    double a = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) a += __ldcg(part + i);
-    const double pq = block_reduce(a);
-    if (threadIdx.x) return;
-    st->pq = pq;
-    if (!(pq > 0.0)) {
-        st->status = ST_BREAKDOWN;
-        st->done = 1;
-        return;
-    }
-    st->alpha = st->rz / pq;
-}
 
 // y = A x over the row panels, one CTA per panel (heaviest panels first).
 // For every chunk of 256 columns the CTA stages the column indices' x values
@@ -373,11 +324,12 @@ __global__ void __launch_bounds__(256) pcg_alpha_kernel(const double* part, int 
 // the last CTA then forms beta and the stopping test, and (fuse_p) also
 // p = z + beta p, which is cheaper than another launch for short vectors.
 // With ypart != nullptr, q_i is the in-order sum of the FP32 product's
-// segment partials (nseg[rowCell[i]] of them).
+// segment partials (nseg[rowCell[i]] of them); with the symmetric packed
+// storage, the in-order sum of its row and column partials (sym_q).
 __global__ void pcg_update_xr_kernel(int64_t n, PcgState* st, double* __restrict__ p,
                                      const double* __restrict__ q, const double* __restrict__ ypart,
                                      const int* __restrict__ rowCell, const int* __restrict__ nseg,
-                                     const double* __restrict__ diag,
+                                     SymPanels sym, const double* __restrict__ diag,
                                      double* x, double* r, double* z, double* part, double tol2, int maxit,
                                      int fuse_p) {
     if (st->done) return;
@@ -385,7 +337,9 @@ __global__ void pcg_update_xr_kernel(int64_t n, PcgState* st, double* __restrict
     double rr = 0.0, rz = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double qi;
-        if (ypart) {
+        if (sym.vals) {
+            qi = sym_q(sym, n, i, 0);
+        } else if (ypart) {
             const int ns = nseg[rowCell[i]];
             qi = 0.0;
             for (int sg = 0; sg < ns; ++sg) qi += ypart[sg * n + i];
@@ -490,7 +444,10 @@ __global__ void seg_reduce_kernel(int64_t n, const int* __restrict__ rowCell, co
 // writes out.
 static void launch_spmv(mlb_ctx* ctx, const double* u, double* out, double* part, PcgState* st,
                         bool sum_in_update = false) {
-    if (ctx->pan.vals32) {
+    if (ctx->sym.vals) {
+        sym_launch(ctx, u, 1, part, st);
+        if (!sum_in_update) sym_reduce(ctx, out);
+    } else if (ctx->pan.vals32) {
         if (ctx->pan.nwork == 0) {    // no wavelet rows: an empty product, a zero dot
             if (part) cudaMemsetAsync(part, 0, sizeof(double), ctx->stream);
             return;
@@ -558,7 +515,7 @@ static mlb_status launch_iteration(mlb_ctx* ctx, double* x, double* r, double* z
         if (s != MLB_OK) return s;
         pcg_alpha_kernel<<<1, 256, 0, st>>>(ctx->partial, kVecBlocks, ctx->pcg);
         ctx->launches += 1;
-    } else if (ctx->pan.vals32 && ctx->pan.nwork == 0) {
+    } else if (!ctx->sym.vals && ctx->pan.vals32 && ctx->pan.nwork == 0) {
         // no wavelet rows: nothing to iterate on
         return MLB_OK;
     } else {
@@ -567,11 +524,13 @@ static mlb_status launch_iteration(mlb_ctx* ctx, double* x, double* r, double* z
         launch_spmv(ctx, p, q, ctx->partial, ctx->pcg, true);
         ctx->launches += 1;
     }
-    const bool segs = !ctx->opts.matrix_free && ctx->pan.vals32;
+    const bool segs = !ctx->opts.matrix_free && !ctx->sym.vals && ctx->pan.vals32;
     // short vectors: the last CTA of the update also forms p; long ones get a launch
     const int fuse_p = n <= kFusePMax ? 1 : 0;
     pcg_update_xr_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, p, q, segs ? ctx->pan.ypart : nullptr,
-                                                     ctx->pan.rowCell, ctx->pan.nseg, diag, x, r, z, part2, tol2,
+                                                     ctx->pan.rowCell, ctx->pan.nseg,
+                                                     ctx->opts.matrix_free ? SymPanels{} : ctx->sym, diag, x, r, z,
+                                                     part2, tol2,
                                                      ctx->opts.pcg_maxit, fuse_p);
     ctx->launches += 1;
     if (!fuse_p) {
@@ -661,7 +620,9 @@ mlb_status solve_dev(mlb_ctx* ctx, const double* Z_kd, mlb_info* info) {
     const std::string pmsg = ctx->err;
     I.nnz = ctx->pan.nnz;
     I.nnz_unique = ctx->pan.nnzUnique;
-    I.col_total = ctx->pan.colTotal;
+    I.col_total = ctx->sym.vals ? 0 : ctx->pan.colTotal;
+    I.symmetric = ctx->sym.vals ? 1 : 0;
+    I.product_values = ctx->opts.matrix_free ? 0 : (ctx->sym.vals ? ctx->sym.stored : ctx->pan.stored);
     I.blocks = ctx->pan.blocks;
     I.ms_assemble = ctx->ms_assemble;
     // gamma = W^T g, then beta
@@ -860,14 +821,15 @@ __global__ void __launch_bounds__(256, 2) spmm_panel_f32_kernel(Panels pan, cons
             if (!st[r].done) pcg_alpha_finish(part + (int64_t)r * gridDim.x, gridDim.x, st + r);
 }
 
-// x_r += alpha_r p_r, r_r -= alpha_r q_r (q_r from the segment partials),
+// x_r += alpha_r p_r, r_r -= alpha_r q_r (q_r from the segment partials, or
+// from the symmetric product's partials),
 // z_r = P^{-1} r_r and the partials of r_r.r_r and r_r.z_r; the last CTA forms
 // beta_r and the stopping test of every recurrence still running.
 __global__ void pcg_update_multi_kernel(int64_t n, PcgState* st, const double* __restrict__ p,
                                         const double* __restrict__ ypart, int nsegMax,
                                         const int* __restrict__ rowCell, const int* __restrict__ nseg,
-                                        const double* __restrict__ diag, double* x, double* rv, double* z,
-                                        double* part, double tol2, int maxit) {
+                                        SymPanels sym, const double* __restrict__ diag, double* x, double* rv,
+                                        double* z, double* part, double tol2, int maxit) {
     if (all_done(st)) return;
     bool act[kRhs];
     double alpha[kRhs], rr[kRhs], rz[kRhs];
@@ -878,12 +840,13 @@ __global__ void pcg_update_multi_kernel(int64_t n, PcgState* st, const double* _
         rr[r] = rz[r] = 0.0;
     }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int ns = nseg[rowCell[i]];
+        const int ns = sym.vals ? 0 : nseg[rowCell[i]];
         const double di = diag ? diag[i] : 1.0;
 #pragma unroll
         for (int r = 0; r < kRhs; ++r) {
             if (!act[r]) continue;
             double qi = 0.0;
+            if (sym.vals) qi = sym_q(sym, n, i, r);
             for (int sg = 0; sg < ns; ++sg) qi += ypart[((int64_t)r * nsegMax + sg) * n + i];
             const int64_t k = r * n + i;
             x[k] += alpha[r] * p[k];
@@ -987,9 +950,13 @@ __global__ void __launch_bounds__(256) pcg_init_multi_scalars(const double* part
     }
 }
 
+// work items of the FP32 product (symmetric storage or row panels)
+static int product_items(const mlb_ctx* ctx) { return ctx->sym.vals ? ctx->sym.nwork : ctx->pan.nwork; }
+
 size_t pcg_multi_work_doubles(const mlb_ctx* ctx) {
     const int64_t n = ctx->nwav;
-    return (size_t)kRhs * (5 * n + (int64_t)ctx->pan.nsegMax * n) + (size_t)kRhs * ctx->pan.nwork +
+    const int64_t nseg = ctx->sym.vals ? 0 : ctx->pan.nsegMax;   // the symmetric partials live in ctx->sym
+    return (size_t)kRhs * (5 * n + nseg * n) + (size_t)kRhs * product_items(ctx) +
            (size_t)2 * kRhs * kVecBlocks + kRhs * (sizeof(PcgState) / sizeof(double) + 1);
 }
 
@@ -997,16 +964,20 @@ size_t pcg_multi_work_doubles(const mlb_ctx* ctx) {
 // panels of the mixed path; work: pcg_multi_work_doubles(ctx) doubles (device).
 // iters (host, kRhs) receives each recurrence's iteration count.
 mlb_status pcg_run_multi(mlb_ctx* ctx, const double* b, double* x, double* work, int* iters) {
-    if (!ctx->pan.vals32 || ctx->opts.matrix_free || ctx->pan.nwork == 0)
+    if (ctx->opts.matrix_free || !(ctx->sym.vals || (ctx->pan.vals32 && ctx->pan.nwork > 0)))
         return fail(ctx, MLB_EINVAL, "several right-hand sides need the assembled FP32 panels");
+    if (ctx->sym.vals) {
+        mlb_status rs = sym_reserve(ctx, kRhs);
+        if (rs != MLB_OK) return rs;
+    }
     cudaStream_t st = ctx->stream;
     const int64_t n = ctx->nwav;
     double* rv = work;
     double* z = rv + kRhs * n;
     double* p = z + kRhs * n;
     double* ypart = p + kRhs * n;
-    double* part = ypart + (int64_t)kRhs * ctx->pan.nsegMax * n;
-    double* part2 = part + (int64_t)kRhs * ctx->pan.nwork;
+    double* part = ypart + (int64_t)kRhs * (ctx->sym.vals ? 0 : ctx->pan.nsegMax) * n;
+    double* part2 = part + (int64_t)kRhs * product_items(ctx);
     PcgState* S = reinterpret_cast<PcgState*>(part2 + 2 * kRhs * kVecBlocks);
     const double* diag = ctx->opts.precond ? ctx->diag : nullptr;
     const double tol2 = ctx->opts.pcg_rtol * ctx->opts.pcg_rtol;
@@ -1025,10 +996,13 @@ mlb_status pcg_run_multi(mlb_ctx* ctx, const double* b, double* x, double* work,
     constexpr int chunk = 8;
     MLB_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < chunk; ++i) {
-        spmm_panel_f32_kernel<<<ctx->pan.nwork, 256, 0, st>>>(ctx->pan, ctx->pan.vals32, ctx->cells.k,
-                                                             ctx->cells.wOff, p, n, ypart, part, S);
+        if (ctx->sym.vals)
+            sym_launch(ctx, p, kRhs, part, S);
+        else
+            spmm_panel_f32_kernel<<<ctx->pan.nwork, 256, 0, st>>>(ctx->pan, ctx->pan.vals32, ctx->cells.k,
+                                                                 ctx->cells.wOff, p, n, ypart, part, S);
         pcg_update_multi_kernel<<<kVecBlocks, 256, 0, st>>>(n, S, p, ypart, ctx->pan.nsegMax, ctx->pan.rowCell,
-                                                            ctx->pan.nseg, diag, x, rv, z, part2, tol2,
+                                                            ctx->pan.nseg, ctx->sym, diag, x, rv, z, part2, tol2,
                                                             ctx->opts.pcg_maxit);
         pcg_update_p_multi_kernel<<<kVecBlocks, 256, 0, st>>>(n, S, z, p);
     }

@@ -66,12 +66,15 @@ def main(argv=None) -> None:
                                   "pairs_per_s": pairs / (ms / 1000.0)}), flush=True)
             else:
                 vb = 4 if prec == "mixed" else 8
+                inf = c.info()
                 # tau = infinity makes the pattern dense: nwav^2 entries.  Algorithmic
-                # bytes: every entry once, u read and C~_W u written.
-                nnz = nw * nw
+                # bytes: every entry the product needs once (each symmetric pair once
+                # when the storage is symmetric), u read and C~_W u written.
+                nnz = inf["nnz_unique"] if inf["symmetric"] else nw * nw
                 algo = nnz * vb + 2 * nw * 8
-                print(json.dumps({"precision": prec, "n": a.n, "nwav": nw, "nnz": nnz, "ms": ms,
-                                  "algorithmic_bytes": algo, "GBps": algo / ms / 1e6}), flush=True)
+                print(json.dumps({"precision": prec, "n": a.n, "nwav": nw, "nnz": nnz,
+                                  "symmetric": inf["symmetric"], "stored_values": inf["product_values"],
+                                  "ms": ms, "algorithmic_bytes": algo, "GBps": algo / ms / 1e6}), flush=True)
         finally:
             c.close()
 
