@@ -325,8 +325,9 @@ def measure(pkg, torch, P, precision, args, dev, local_rank, world, stream):
     vb = 4 if precision == "mixed" else 8
     if info.get("symmetric"):
         # symmetric storage: the algorithmic bytes of one product are the
-        # unique entries (blocks j >= i) once, x read and y written once
-        out["spmv_kernel"] = "sym_spmv_f32_kernel"
+        # unique entries (blocks j >= i) once, x read and y written once;
+        # the form of the product is the one the library's autotuner kept
+        out["spmv_kernel"] = "sym_spmv_bulk_kernel" if info.get("product_variant") == 1 else "sym_spmv_f32_kernel"
         out["spmv_bytes"] = info["nnz_unique"] * 4 + 2 * nwav * 8
     else:
         # row panels: every stored value once, each panel's column list once,

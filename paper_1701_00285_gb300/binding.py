@@ -43,7 +43,8 @@ class Info(ctypes.Structure):
                 ("nnz", ctypes.c_int64), ("blocks", ctypes.c_int64), ("ms_assemble", ctypes.c_double),
                 ("ms_pcg", ctypes.c_double), ("ms_beta", ctypes.c_double),
                 ("nnz_unique", ctypes.c_int64), ("launches", ctypes.c_int64), ("col_total", ctypes.c_int64),
-                ("product_values", ctypes.c_int64), ("symmetric", ctypes.c_int)]
+                ("product_values", ctypes.c_int64), ("symmetric", ctypes.c_int),
+                ("product_variant", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -93,6 +94,7 @@ _SIGS = {
     "mlb_cw_matvec_dev": (ctypes.c_int, [_P, _P, _P]),
     "mlb_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "mlb_get_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    "mlb_set_product_variant": (ctypes.c_int, [_P, ctypes.c_int]),
     "mlb_apply_W_noalloc": (ctypes.c_int, [_P, _P, _P]),
     "mlb_get_pattern": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "mlb_kernel_sum": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
@@ -338,6 +340,10 @@ class Context:
         info = Info()
         self._check(lib().mlb_get_info(self._h, ctypes.byref(info)))
         return info.as_dict()
+
+    def set_product_variant(self, variant: int):
+        """Forces the form of the symmetric FP32 product (0 loads, 1 bulk copies)."""
+        self._check(lib().mlb_set_product_variant(self._h, variant))
 
     def launch_count(self) -> int:
         c = _I64()

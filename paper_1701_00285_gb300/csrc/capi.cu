@@ -641,8 +641,18 @@ mlb_status mlb_apply_Wt(mlb_ctx* ctx, const double* u, double* out) {
 mlb_status mlb_cw_matvec(mlb_ctx* ctx, const double* u, double* out) {
     if (!ctx || !u || !out) return fail(ctx, MLB_EINVAL, "null argument");
     if (ctx->state < 2) return fail(ctx, MLB_ESTATE, "no assembly");
-    return host_roundtrip(ctx, u, ctx->nwav, out, ctx->nwav,
-                          [&](double* din, double* dout) { return cw_matvec_dev(ctx, din, dout); });
+    mlb_status s = host_roundtrip(ctx, u, ctx->nwav, out, ctx->nwav,
+                                  [&](double* din, double* dout) { return cw_matvec_dev(ctx, din, dout); });
+    if (s == MLB_OK && ctx->sym.err) {
+        // the product's bounded waits report here (host_roundtrip has synchronised)
+        int e = 0;
+        MLB_CUDA(ctx, cudaMemcpy(&e, ctx->sym.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            MLB_CUDA(ctx, cudaMemset(ctx->sym.err, 0, sizeof(int)));
+            return fail(ctx, MLB_ETIMEOUT, "a bounded wait of the matrix product gave up");
+        }
+    }
+    return s;
 }
 
 mlb_status mlb_cw_matvec_dev(mlb_ctx* ctx, const double* u_dev, double* out_dev) {
@@ -665,7 +675,16 @@ mlb_status mlb_get_info(const mlb_ctx* ctx, mlb_info* info) {
     I.product_values = ctx->opts.matrix_free ? 0 : (ctx->sym.vals ? ctx->sym.stored : ctx->pan.stored);
     I.ms_assemble = ctx->ms_assemble;
     I.launches = ctx->launches;
+    I.product_variant = ctx->sym.vals ? ctx->sym_variant : 0;
     *info = I;
+    return MLB_OK;
+}
+
+mlb_status mlb_set_product_variant(mlb_ctx* ctx, int variant) {
+    if (!ctx) return MLB_EINVAL;
+    if (ctx->state < 2 || !ctx->sym.vals) return fail(ctx, MLB_ESTATE, "no symmetric storage in this assembly");
+    if (variant != 0 && variant != 1) return fail(ctx, MLB_EINVAL, "variant must be 0 or 1");
+    ctx->sym_variant = variant;
     return MLB_OK;
 }
 

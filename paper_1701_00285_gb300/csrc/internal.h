@@ -71,29 +71,36 @@ constexpr int kSegCols = 8192;
 // Upper bound on the FP32 product's work items: the cells hold nwav <= N rows
 // and at most N columns, so the count is at most
 // (ncell + N / kItemRows) x ceil(N / kSegCols).
+// The symmetric product's items (sym_plan, at least 512 columns each) number
+// at most ceil(N / 128) x (ceil(N / 512) + 1); the bound covers both.
 inline size_t max_work_items(int ncell, int64_t N) {
-    return ((size_t)ncell + (size_t)(N / kItemRows) + 1) * (size_t)((N + kSegCols - 1) / kSegCols);
+    const size_t panels = ((size_t)ncell + (size_t)(N / kItemRows) + 1) * (size_t)((N + kSegCols - 1) / kSegCols);
+    const size_t sym = (size_t)((N + 127) / 128) * (size_t)((N + 511) / 512 + 1);
+    return panels > sym ? panels : sym;
 }
 
 // Symmetric packed storage of a complete C~_W in FP32 (mixed path, every
 // cell pair admissible): each symmetric pair of entries is stored once.  The
 // wavelet rows are grouped in blocks of kSymRows; block b keeps its rows from
 // its own first column (b kSymRows) to the last, i.e. its diagonal square in
-// full and everything to the right of it, row-major with the row stride
-// sym_width(nwav, b) (a multiple of 4, zero padded).  The product streams
-// every stored value once and applies it twice (B x to the block's rows and
-// B^T x to the columns' rows).  Work items are (block, segment of kSymSeg
-// columns), heaviest first; an item's row sums go to rowpart (by segment) and
-// its column sums to colpart (by block), both summed in a fixed order by the
-// consumer, so the product is deterministic.
+// full and everything to the right of it, over sym_width(nwav, b) columns (a
+// multiple of kSymTile, zero padded).  Those columns are cut into tiles of
+// kSymTile columns, each stored contiguously (the block's rows one after the
+// other, kSymTile values each), so one tile is one contiguous copy.  The
+// product streams every stored value once and applies it twice (B x to the
+// block's rows and B^T x to the columns' rows).  Work items are (block,
+// segment of `seg` columns, a multiple of 256 chosen by the autotuner),
+// heaviest first; an item's row sums go to
+// rowpart (by segment) and its column sums to colpart (by block), both summed
+// in a fixed order by the consumer, so the product is deterministic.
 constexpr int kSymRows = 128;
-constexpr int kSymSeg = 2048;
+constexpr int kSymTile = 64;
 
 __host__ __device__ inline int64_t sym_width(int64_t nwav, int b) {
-    return ((nwav - (int64_t)b * kSymRows) + 3) & ~(int64_t)3;
+    return ((nwav - (int64_t)b * kSymRows) + kSymTile - 1) / kSymTile * kSymTile;
 }
-__host__ __device__ inline int sym_nseg(int64_t nwav, int b) {
-    return (int)((sym_width(nwav, b) + kSymSeg - 1) / kSymSeg);
+__host__ __device__ inline int sym_nseg(int64_t nwav, int b, int seg) {
+    return (int)((sym_width(nwav, b) + seg - 1) / seg);
 }
 
 struct SymPanels {
@@ -103,10 +110,17 @@ struct SymPanels {
     int64_t* off = nullptr;     // per block: offset of its first value
     int2* work = nullptr;       // (block, segment), heaviest first
     int nwork = 0;
+    int nworkCap = 0;
+    int seg = 0;                // columns per work item
     int nsegMax = 0;
+    int nsegCap = 0;            // segments the row-partial buffer holds per right-hand side
     int nrhs = 0;               // right-hand sides the partial buffers hold
-    double* rowpart = nullptr;  // nrhs x nsegMax x nwav
-    double* colpart = nullptr;  // nrhs x nblk x nwav
+    float* rowpart = nullptr;   // nrhs x nsegCap x nwav (FP32 sums)
+    float* colpart = nullptr;   // nrhs x nblk x nwav
+    float* xh = nullptr;        // nrhs x xld: FP32 high parts of the vectors multiplied
+    float* xl = nullptr;        //             and their low parts (x = h + l to about 2^-48)
+    int64_t xld = 0;            // nwav rounded up past the widest padded row, zero beyond nwav
+    int* err = nullptr;         // device flag: bit 0 set when a bounded wait of the product gave up
 };
 
 struct PcgState {
@@ -164,6 +178,7 @@ struct mlb_ctx {
     mlb::Panels pan;
     mlb::SymPanels sym;            // mixed path, complete pattern: each symmetric pair stored once
     bool allow_sym = true;         // false: keep the FP32 row panels instead (batched small systems)
+    int sym_variant = 0;           // form of the symmetric product (autotuned): 0 loads, 1 bulk-copy pipeline
     double* diag = nullptr;        // diag(C~_W)
     double ms_assemble = 0;
     mlb::Arena arena_asm;
@@ -221,8 +236,10 @@ mlb_status build_sym(mlb_ctx* ctx);
 // partial buffers for nrhs simultaneous products (grown on demand)
 mlb_status sym_reserve(mlb_ctx* ctx, int nrhs);
 // products of the nrhs vectors x (nrhs x nwav) into the partial buffers; part
-// (nrhs x nwork) and st (nrhs states) may be nullptr outside the PCG
-void sym_launch(mlb_ctx* ctx, const double* x, int nrhs, double* part, PcgState* st);
+// (nrhs x nwork) and st (nrhs states) may be nullptr outside the PCG.
+// presplit: the FP32 parts of x are already in ctx->sym.xh / xl (the PCG's
+// vector updates write them)
+void sym_launch(mlb_ctx* ctx, const double* x, int nrhs, double* part, PcgState* st, bool presplit = false);
 // out = the sums of the partials of right-hand side 0
 void sym_reduce(mlb_ctx* ctx, double* out);
 // solve.cu

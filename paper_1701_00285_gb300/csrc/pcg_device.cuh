@@ -9,7 +9,7 @@ namespace mlb {
 
 constexpr int kVecBlocks = 512;
 
-enum { ST_OK = 0, ST_BREAKDOWN = 1, ST_NOCONV = 2 };
+enum { ST_OK = 0, ST_BREAKDOWN = 1, ST_NOCONV = 2, ST_TIMEOUT = 3 };
 
 static __device__ double block_reduce(double v) {
     __shared__ double red[32];
@@ -65,12 +65,12 @@ static __device__ void pcg_alpha_finish(const double* part, int nparts, PcgState
 // always in this order, so the result does not depend on scheduling.
 static __device__ __forceinline__ double sym_q(const SymPanels& S, int64_t n, int64_t i, int rhs) {
     const int b = (int)(i / kSymRows);
-    const int ns = sym_nseg(n, b);
-    const double* rp = S.rowpart + (int64_t)rhs * S.nsegMax * n + i;
+    const int ns = sym_nseg(n, b, S.seg);
+    const float* rp = S.rowpart + (int64_t)rhs * S.nsegCap * n + i;
     double q = 0.0;
-    for (int s = 0; s < ns; ++s) q += rp[(int64_t)s * n];
-    const double* cp = S.colpart + (int64_t)rhs * S.nblk * n + i;
-    for (int c = 0; c < b; ++c) q += cp[(int64_t)c * n];
+    for (int s = 0; s < ns; ++s) q += (double)rp[(int64_t)s * n];
+    const float* cp = S.colpart + (int64_t)rhs * S.nblk * n + i;
+    for (int c = 0; c < b; ++c) q += (double)cp[(int64_t)c * n];
     return q;
 }
 

@@ -25,6 +25,20 @@ namespace mlb {
 
 constexpr int64_t kFusePMax = 16384;   // longest vector whose p update the last CTA does
 
+// The symmetric FP32 product reads its vector as FP32 high and low parts
+// (SymPanels::xh, xl); the kernels that write the PCG direction p also write
+// those parts, so the product needs no conversion launch of its own.
+__device__ __forceinline__ void store_split(float* xh, float* xl, int64_t k, double v) {
+    if (!xh) return;
+    const float h = (float)v;
+    xh[k] = h;
+    xl[k] = (float)(v - (double)h);
+}
+
+// the split buffers of the context's product, or nullptr when it reads none
+static float* split_h(const mlb_ctx* ctx) { return (ctx->sym.vals && !ctx->opts.matrix_free) ? ctx->sym.xh : nullptr; }
+static float* split_l(const mlb_ctx* ctx) { return (ctx->sym.vals && !ctx->opts.matrix_free) ? ctx->sym.xl : nullptr; }
+
 // y = A x over the row panels, one CTA per panel (heaviest panels first).
 // For every chunk of 256 columns the CTA stages the column indices' x values
 // once in shared memory; each warp then streams its rows' values and
@@ -264,7 +278,7 @@ __global__ void __launch_bounds__(256, 4) spmv_panel_f32_kernel(Panels pan, cons
 
 // x = 0, r = b, z = r / diag, p = z; partials of r.z and b.b
 __global__ void pcg_init_kernel(int64_t n, const double* __restrict__ b, const double* __restrict__ diag,
-                                double* x, double* r, double* z, double* p, double* part) {
+                                double* x, double* r, double* z, double* p, double* part, float* xh, float* xl) {
     double rz = 0.0, bb = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double bi = b[i];
@@ -273,6 +287,7 @@ __global__ void pcg_init_kernel(int64_t n, const double* __restrict__ b, const d
         r[i] = bi;
         z[i] = zi;
         p[i] = zi;
+        store_split(xh, xl, i, zi);
         rz += bi * zi;
         bb += bi * bi;
     }
@@ -331,7 +346,7 @@ __global__ void pcg_update_xr_kernel(int64_t n, PcgState* st, double* __restrict
                                      const int* __restrict__ rowCell, const int* __restrict__ nseg,
                                      SymPanels sym, const double* __restrict__ diag,
                                      double* x, double* r, double* z, double* part, double tol2, int maxit,
-                                     int fuse_p) {
+                                     int fuse_p, float* xh, float* xl) {
     if (st->done) return;
     const double alpha = st->alpha;
     double rr = 0.0, rz = 0.0;
@@ -388,14 +403,22 @@ __global__ void pcg_update_xr_kernel(int64_t n, PcgState* st, double* __restrict
     }
     __syncthreads();
     if (fuse_p && go_on)
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = __ldcg(z + i) + beta_s * p[i];
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const double v = __ldcg(z + i) + beta_s * p[i];
+            p[i] = v;
+            store_split(xh, xl, i, v);
+        }
 }
 
-__global__ void pcg_update_p_kernel(int64_t n, PcgState* st, const double* __restrict__ z, double* p) {
+__global__ void pcg_update_p_kernel(int64_t n, PcgState* st, const double* __restrict__ z, double* p, float* xh,
+                                    float* xl) {
     if (st->done) return;
     const double beta = st->beta;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = z[i] + beta * p[i];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = z[i] + beta * p[i];
+        p[i] = v;
+        store_split(xh, xl, i, v);
+    }
 }
 
 // resid = Z - C gamma - eta gamma, then partial sums of X^T resid
@@ -445,7 +468,8 @@ __global__ void seg_reduce_kernel(int64_t n, const int* __restrict__ rowCell, co
 static void launch_spmv(mlb_ctx* ctx, const double* u, double* out, double* part, PcgState* st,
                         bool sum_in_update = false) {
     if (ctx->sym.vals) {
-        sym_launch(ctx, u, 1, part, st);
+        // inside the PCG the vector updates have already split p
+        sym_launch(ctx, u, 1, part, st, sum_in_update);
         if (!sum_in_update) sym_reduce(ctx, out);
     } else if (ctx->pan.vals32) {
         if (ctx->pan.nwork == 0) {    // no wavelet rows: an empty product, a zero dot
@@ -531,10 +555,10 @@ static mlb_status launch_iteration(mlb_ctx* ctx, double* x, double* r, double* z
                                                      ctx->pan.rowCell, ctx->pan.nseg,
                                                      ctx->opts.matrix_free ? SymPanels{} : ctx->sym, diag, x, r, z,
                                                      part2, tol2,
-                                                     ctx->opts.pcg_maxit, fuse_p);
+                                                     ctx->opts.pcg_maxit, fuse_p, split_h(ctx), split_l(ctx));
     ctx->launches += 1;
     if (!fuse_p) {
-        pcg_update_p_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, z, p);
+        pcg_update_p_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, z, p, split_h(ctx), split_l(ctx));
         ctx->launches += 1;
     }
     return MLB_OK;
@@ -550,7 +574,7 @@ mlb_status pcg_run(mlb_ctx* ctx, const double* b, double* x, mlb_info* info) {
     double* p = ctx->vec + 3 * n;
     double* q = ctx->vec + 4 * n;
     const double* diag = ctx->opts.precond ? ctx->diag : nullptr;
-    pcg_init_kernel<<<kVecBlocks, 256, 0, st>>>(n, b, diag, x, r, z, p, ctx->partial);
+    pcg_init_kernel<<<kVecBlocks, 256, 0, st>>>(n, b, diag, x, r, z, p, ctx->partial, split_h(ctx), split_l(ctx));
     pcg_init_scalars<<<1, 256, 0, st>>>(ctx->partial, ctx->pcg);
     MLB_CHECK_LAUNCH(ctx, "pcg_init");
     ctx->launches += 1;
@@ -605,6 +629,7 @@ mlb_status pcg_run(mlb_ctx* ctx, const double* b, double* x, mlb_info* info) {
     }
     if (hs.status == ST_BREAKDOWN) return fail(ctx, MLB_EBREAKDOWN, "PCG breakdown: p^T C~_W p <= 0");
     if (hs.status == ST_NOCONV) return fail(ctx, MLB_ENOCONV, "PCG did not reach pcg_rtol within pcg_maxit");
+    if (hs.status == ST_TIMEOUT) return fail(ctx, MLB_ETIMEOUT, "a bounded wait of the matrix product gave up");
     return MLB_OK;
 }
 
@@ -622,6 +647,7 @@ mlb_status solve_dev(mlb_ctx* ctx, const double* Z_kd, mlb_info* info) {
     I.nnz_unique = ctx->pan.nnzUnique;
     I.col_total = ctx->sym.vals ? 0 : ctx->pan.colTotal;
     I.symmetric = ctx->sym.vals ? 1 : 0;
+    I.product_variant = ctx->sym.vals ? ctx->sym_variant : 0;
     I.product_values = ctx->opts.matrix_free ? 0 : (ctx->sym.vals ? ctx->sym.stored : ctx->pan.stored);
     I.blocks = ctx->pan.blocks;
     I.ms_assemble = ctx->ms_assemble;
@@ -892,16 +918,22 @@ __global__ void pcg_update_multi_kernel(int64_t n, PcgState* st, const double* _
     }
 }
 
-__global__ void pcg_update_p_multi_kernel(int64_t n, const PcgState* st, const double* __restrict__ z, double* p) {
+__global__ void pcg_update_p_multi_kernel(int64_t n, const PcgState* st, const double* __restrict__ z, double* p,
+                                          float* xh, float* xl, int64_t xld) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
 #pragma unroll
         for (int r = 0; r < kRhs; ++r)
-            if (!st[r].done) p[r * n + i] = z[r * n + i] + st[r].beta * p[r * n + i];
+            if (!st[r].done) {
+                const double v = z[r * n + i] + st[r].beta * p[r * n + i];
+                p[r * n + i] = v;
+                store_split(xh, xl, r * xld + i, v);
+            }
 }
 
 // x_r = 0, r_r = b_r, z_r = P^{-1} b_r, p_r = z_r; the scalars of every recurrence
 __global__ void pcg_init_multi_kernel(int64_t n, const double* __restrict__ b, const double* __restrict__ diag,
-                                      double* x, double* rv, double* z, double* p, double* part) {
+                                      double* x, double* rv, double* z, double* p, double* part, float* xh, float* xl,
+                                      int64_t xld) {
     double rz[kRhs], bb[kRhs];
 #pragma unroll
     for (int r = 0; r < kRhs; ++r) rz[r] = bb[r] = 0.0;
@@ -915,6 +947,7 @@ __global__ void pcg_init_multi_kernel(int64_t n, const double* __restrict__ b, c
             rv[k] = bi;
             z[k] = zi;
             p[k] = zi;
+            store_split(xh, xl, r * xld + i, zi);
             rz[r] += bi * zi;
             bb[r] += bi * bi;
         }
@@ -981,7 +1014,8 @@ mlb_status pcg_run_multi(mlb_ctx* ctx, const double* b, double* x, double* work,
     PcgState* S = reinterpret_cast<PcgState*>(part2 + 2 * kRhs * kVecBlocks);
     const double* diag = ctx->opts.precond ? ctx->diag : nullptr;
     const double tol2 = ctx->opts.pcg_rtol * ctx->opts.pcg_rtol;
-    pcg_init_multi_kernel<<<kVecBlocks, 256, 0, st>>>(n, b, diag, x, rv, z, p, part2);
+    pcg_init_multi_kernel<<<kVecBlocks, 256, 0, st>>>(n, b, diag, x, rv, z, p, part2, split_h(ctx), split_l(ctx),
+                                                      ctx->sym.xld);
     pcg_init_multi_scalars<<<1, 256, 0, st>>>(part2, S);
     MLB_CHECK_LAUNCH(ctx, "pcg_init_multi");
     ctx->launches += 1;
@@ -997,14 +1031,14 @@ mlb_status pcg_run_multi(mlb_ctx* ctx, const double* b, double* x, double* work,
     MLB_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < chunk; ++i) {
         if (ctx->sym.vals)
-            sym_launch(ctx, p, kRhs, part, S);
+            sym_launch(ctx, p, kRhs, part, S, true);
         else
             spmm_panel_f32_kernel<<<ctx->pan.nwork, 256, 0, st>>>(ctx->pan, ctx->pan.vals32, ctx->cells.k,
                                                                  ctx->cells.wOff, p, n, ypart, part, S);
         pcg_update_multi_kernel<<<kVecBlocks, 256, 0, st>>>(n, S, p, ypart, ctx->pan.nsegMax, ctx->pan.rowCell,
                                                             ctx->pan.nseg, ctx->sym, diag, x, rv, z, part2, tol2,
                                                             ctx->opts.pcg_maxit);
-        pcg_update_p_multi_kernel<<<kVecBlocks, 256, 0, st>>>(n, S, z, p);
+        pcg_update_p_multi_kernel<<<kVecBlocks, 256, 0, st>>>(n, S, z, p, split_h(ctx), split_l(ctx), ctx->sym.xld);
     }
     MLB_CUDA(ctx, cudaStreamEndCapture(st, &own.graph));
     MLB_CUDA(ctx, cudaGraphInstantiate(&own.exec, own.graph, 0));
@@ -1022,6 +1056,8 @@ mlb_status pcg_run_multi(mlb_ctx* ctx, const double* b, double* x, double* work,
         if (iters) iters[r] = hs[r].it;
         if (hs[r].status == ST_BREAKDOWN) return fail(ctx, MLB_EBREAKDOWN, "PCG breakdown: p^T C~_W p <= 0");
         if (hs[r].status == ST_NOCONV) return fail(ctx, MLB_ENOCONV, "PCG did not reach pcg_rtol within pcg_maxit");
+        if (hs[r].status == ST_TIMEOUT)
+            return fail(ctx, MLB_ETIMEOUT, "a bounded wait of the matrix product gave up");
     }
     return MLB_OK;
 }

@@ -9,10 +9,13 @@
 // if both triangles were stored.  Here each symmetric pair is stored once:
 //
 //   rows in blocks of kSymRows; block b keeps columns b kSymRows .. nwav - 1
-//   (its diagonal square in full, and everything to the right of it),
-//   row-major, row stride sym_width(nwav, b).
+//   (its diagonal square in full, and everything to the right of it), cut
+//   into tiles of kSymTile columns, each tile stored contiguously with the
+//   block's rows one after the other (row r, column c of block b at
+//   off[b] + (c / kSymTile) rows kSymTile + r kSymTile + c % kSymTile,
+//   c counted from b kSymRows).
 //
-// One CTA per work item (block b, segment of kSymSeg columns) streams its
+// One CTA per work item (block b, segment of S.seg columns) streams its
 // values once and applies each value twice: to the block's rows (B x, row
 // sums) and, for the columns right of the diagonal square, to the columns'
 // rows (B^T x, column sums).  Row sums go to rowpart[segment], column sums to
@@ -21,9 +24,12 @@
 // PCG needs is linear in the partials, so every item adds its share and the
 // last CTA of the launch forms alpha as on the row-panel path.
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <utility>
 #include <vector>
 
+#include "bulk.cuh"
 #include "internal.h"
 #include "pcg_device.cuh"
 
@@ -43,11 +49,12 @@ __global__ void sym_pack_kernel(Panels pan, const int* __restrict__ rowCell, con
         const int64_t row0 = (int64_t)b * kSymRows;
         const int64_t W = sym_width(n, b);
         const int g = rowCell[i];
+        const int64_t rows = min((int64_t)kSymRows, n - row0);
         const double* src = pan.vals + pan.valOff[g] + (i - wOff[g]) * (int64_t)pan.ncols[g];
-        float* dst = S.vals + S.off[b] + (i - row0) * W;
+        float* dst = S.vals + S.off[b] + (i - row0) * kSymTile;
         for (int64_t c = lane; c < W; c += 32) {
             const int64_t j = row0 + c;
-            dst[c] = j < n ? (float)src[j] : 0.0f;
+            dst[(c / kSymTile) * rows * kSymTile + c % kSymTile] = j < n ? (float)src[j] : 0.0f;
         }
     }
 }
@@ -64,7 +71,9 @@ __global__ void sym_pack_kernel(Panels pan, const int* __restrict__ rowCell, con
 // and to the column sum (against the staged x of the row).  x enters as FP32
 // high and low parts (x = h + l to about 2^-48), products and sums are FP32,
 // and the partials leave in FP64.  Column sums cross the eight warps through
-// a double-buffered shared array, so one barrier per chunk remains.  One
+// a double-buffered shared array, so one barrier per chunk remains.  The
+// partials are FP32 sums and are stored as such (FP64 storage would add
+// bytes, not digits); the consumer adds them in FP64.  One
 // thread per row asks the L2 for that row's next chunk (bulk prefetch) while
 // the current one is multiplied.
 __global__ void __launch_bounds__(256, 2) sym_spmv_f32_kernel(SymPanels S, int64_t n, const double* __restrict__ x,
@@ -86,12 +95,13 @@ __global__ void __launch_bounds__(256, 2) sym_spmv_f32_kernel(SymPanels S, int64
     const int64_t row0 = (int64_t)b * kSymRows;
     const int rows = (int)min((int64_t)kSymRows, n - row0);
     const int64_t W = sym_width(n, b);
-    const int64_t cs = row0 + (int64_t)wk.y * kSymSeg;      // first column of the item
-    const int64_t ce = min(row0 + W, cs + kSymSeg);          // end of its columns (padded width)
+    const int64_t cs = row0 + (int64_t)wk.y * S.seg;      // first column of the item
+    const int64_t ce = min(row0 + W, cs + S.seg);          // end of its columns (padded width)
     const int64_t diagEnd = row0 + kSymRows;                 // columns below: the diagonal square
     const double* __restrict__ xv = x + (int64_t)rhs * n;
-    const float* __restrict__ vb = S.vals + S.off[b];        // row r, column c: vb[r W + c - row0]
-    double* __restrict__ colpart = S.colpart + ((int64_t)rhs * S.nblk + b) * n;
+    const float* __restrict__ vb = S.vals + S.off[b];        // the block's first tile
+    const int64_t tstride = (int64_t)rows * kSymTile;         // values per tile
+    float* __restrict__ colpart = S.colpart + ((int64_t)rhs * S.nblk + b) * n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < kSymRows) {
         const double xr = tid < rows ? xv[row0 + tid] : 0.0;
@@ -116,11 +126,11 @@ __global__ void __launch_bounds__(256, 2) sym_spmv_f32_kernel(SymPanels S, int64
     for (int64_t c0 = cs; c0 < ce; c0 += CH) {
         const int m = (int)min((int64_t)CH, ce - c0);          // a multiple of 4
         const int64_t pc = c0 + CH;
-        // rows start 16-byte aligned and the chunk is a multiple of 4 values,
-        // as the bulk prefetch requires
-        if (tid < rows && pc < ce)
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(vb + (int64_t)tid * W + (pc - row0)),
-                         "r"((unsigned)(min((int64_t)CH, ce - pc) * 4))
+        // the next chunk's tiles, one contiguous bulk prefetch each (tiles
+        // start 16-byte aligned and hold a multiple of 4 values)
+        if (tid < (int)min((int64_t)(CH / kSymTile), (ce - pc) / kSymTile))
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(vb + ((pc - row0) / kSymTile + tid) * tstride),
+                         "r"((unsigned)(tstride * 4))
                          : "memory");
         const int64_t cn = pc + tid;
         const double xn = (cn < ce && cn < n) ? xv[cn] : 0.0;
@@ -129,7 +139,10 @@ __global__ void __launch_bounds__(256, 2) sym_spmv_f32_kernel(SymPanels S, int64
         const float4 l0 = *reinterpret_cast<const float4*>(&xcl[buf][j0]);
         const float4 h1 = *reinterpret_cast<const float4*>(&xch[buf][j1]);
         const float4 l1 = *reinterpret_cast<const float4*>(&xcl[buf][j1]);
-        const float* vc = vb + (c0 - row0);
+        // lane columns 4 lane and 128 + 4 lane of the chunk: tiles lane / 16
+        // and 2 + lane / 16 of it, column 4 (lane % 16) of the tile
+        const float* vc0 = vb + ((c0 - row0) / kSymTile + (lane >> 4)) * tstride + 4 * (lane & 15);
+        const float* vc1 = vc0 + 2 * tstride;
         float ca[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) ca[k] = 0.0f;
@@ -139,9 +152,8 @@ __global__ void __launch_bounds__(256, 2) sym_spmv_f32_kernel(SymPanels S, int64
 #pragma unroll
             for (int q = 0; q < G; ++q) {
                 const int r = min(warp + 8 * (k0 + q), rows - 1);
-                const float* rp = vc + (int64_t)r * W;
-                v[q][0] = ok0 ? __ldg(reinterpret_cast<const float4*>(rp + j0)) : make_float4(0.f, 0.f, 0.f, 0.f);
-                v[q][1] = ok1 ? __ldg(reinterpret_cast<const float4*>(rp + j1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                v[q][0] = ok0 ? __ldg(reinterpret_cast<const float4*>(vc0 + r * kSymTile)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                v[q][1] = ok1 ? __ldg(reinterpret_cast<const float4*>(vc1 + r * kSymTile)) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
             for (int q = 0; q < G; ++q) {
@@ -180,12 +192,12 @@ __global__ void __launch_bounds__(256, 2) sym_spmv_f32_kernel(SymPanels S, int64
 #pragma unroll
             for (int w = 0; w < 8; ++w) s += cred[buf][w][tid];
             const double sd = (double)s;
-            colpart[c] = sd;
+            colpart[c] = s;
             dotp += xv[c] * sd;
         }
         buf ^= 1;
     }
-    double* __restrict__ rowpart = S.rowpart + ((int64_t)rhs * S.nsegMax + wk.y) * n;
+    float* __restrict__ rowpart = S.rowpart + ((int64_t)rhs * S.nsegCap + wk.y) * n;
 #pragma unroll
     for (int k = 0; k < RW; ++k) {
         float a = racc[k];
@@ -193,7 +205,7 @@ __global__ void __launch_bounds__(256, 2) sym_spmv_f32_kernel(SymPanels S, int64
         const int r = warp + 8 * k;
         if (lane == 0 && r < rows) {
             const double q = (double)a;
-            rowpart[row0 + r] = q;
+            rowpart[row0 + r] = a;
             dotp += xv[row0 + r] * q;
         }
     }
@@ -206,24 +218,282 @@ __global__ void __launch_bounds__(256, 2) sym_spmv_f32_kernel(SymPanels S, int64
     }
 }
 
+// ---- the same product as a bulk-copy pipeline ------------------------------
+//
+// One producer warp streams the item through a ring of kStages shared-memory
+// stages, each one tile (128 rows x kStCols columns, contiguous in global
+// memory: a single 32 KB bulk copy) plus the matching FP32 high and low parts
+// of x, completion counted in bytes on the stage's "full" mbarrier.  Eight
+// consumer warps take the stages in order; warp w owns rows w + 8k and every
+// lane two columns of the stage, so a warp reads 256 contiguous bytes of a
+// row per shared load.  The values reach shared memory without passing
+// through registers, so the bytes in flight are set by the ring (three 33 KB
+// stages per CTA, two CTAs per SM), not by the consumers' registers.
+// Each consumer warp leaves its column sums of a stage in its own row of the
+// stage's column array and releases the stage on its "empty" mbarrier; the
+// producer, which waits for that release before refilling the slot anyway,
+// adds the eight warps' column sums in a fixed order and writes them out, so
+// the consumers never wait for one another.  Every wait is bounded
+// (bulk.cuh): one that gives up sets bit 0 of S.err (and, inside the PCG, the
+// status ST_TIMEOUT), and the producer then waits (bounded) for its copies in
+// flight before the CTA ends.
+constexpr int kStCols = kSymTile;   // one stage = one tile of the block
+constexpr int kStages = 3;
+constexpr int kStageFloats = kSymRows * kStCols + 2 * kStCols;
+constexpr size_t kBulkSmem = sizeof(float) * ((size_t)kStages * kStageFloats + (size_t)kStages * 8 * kStCols) +
+                             sizeof(uint64_t) * 2 * kStages;
+
+// x (nrhs x n, FP64) -> FP32 high and low parts (nrhs x xld, zero past n)
+__global__ void xsplit_kernel(int64_t n, int nrhs, const double* __restrict__ x, int64_t xld, float* __restrict__ xh,
+                              float* __restrict__ xl, const PcgState* st) {
+    const int64_t tot = (int64_t)nrhs * xld;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < tot; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = k / xld, i = k - r * xld;
+        if (st && st[r].done) continue;
+        const double v = i < n ? x[r * n + i] : 0.0;
+        const float h = (float)v;
+        xh[k] = h;
+        xl[k] = (float)(v - (double)h);
+    }
+}
+
+__device__ __forceinline__ void set_timeout(const SymPanels& S, PcgState* ps) {
+    atomicOr(S.err, 1);
+    if (ps) {
+        ps->status = ST_TIMEOUT;
+        ps->done = 1;
+    }
+}
+
+__global__ void __launch_bounds__(288, 2) sym_spmv_bulk_kernel(SymPanels S, int64_t n, const double* __restrict__ x,
+                                                             int nrhs, double* __restrict__ part, PcgState* st) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float* stg = reinterpret_cast<float*>(smraw);                             // kStages x kStageFloats
+    float* cred = stg + kStages * kStageFloats;                               // [kStages][8][kStCols]
+    uint64_t* full = reinterpret_cast<uint64_t*>(cred + kStages * 8 * kStCols);
+    uint64_t* empty = full + kStages;
+    const int rhs = (int)(blockIdx.x % (unsigned)nrhs);
+    const int item = (int)(blockIdx.x / (unsigned)nrhs);
+    PcgState* ps = st ? st + rhs : nullptr;
+    if (ps && ps->done) return;
+    const int2 wk = S.work[item];
+    const int b = wk.x;
+    const int64_t row0 = (int64_t)b * kSymRows;
+    const int rows = (int)min((int64_t)kSymRows, n - row0);
+    const int64_t W = sym_width(n, b);
+    const int64_t cs = row0 + (int64_t)wk.y * S.seg;
+    const int64_t ce = min(row0 + W, cs + S.seg);
+    const int64_t diagEnd = row0 + kSymRows;
+    const int nst = (int)((ce - cs) / kStCols);                                // whole tiles
+    const double* __restrict__ xv = x + (int64_t)rhs * n;
+    const float* __restrict__ xh = S.xh + (int64_t)rhs * S.xld;
+    const float* __restrict__ xl = S.xl + (int64_t)rhs * S.xld;
+    const float* __restrict__ vb = S.vals + S.off[b];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int k = 0; k < kStages; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], 8);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    double dotp = 0.0;
+    if (warp == 8) {
+        // producer.  Tiles start 16-byte aligned and hold a multiple of 16
+        // bytes, as the bulk copy requires.
+        float* __restrict__ colpart = S.colpart + ((int64_t)rhs * S.nblk + b) * n;
+        // column sums of stage s (its slot released by all eight warps): the
+        // warps' sums in order, the x of the columns from the stage itself
+        auto finish = [&](int s) {
+            const int slot = s % kStages;
+            const float* cr = cred + slot * 8 * kStCols + 2 * lane;
+            float2 a = *reinterpret_cast<const float2*>(cr);
+#pragma unroll
+            for (int w = 1; w < 8; ++w) {
+                const float2 t = *reinterpret_cast<const float2*>(cr + w * kStCols);
+                a.x += t.x;
+                a.y += t.y;
+            }
+            const float* sx = stg + slot * kStageFloats + kSymRows * kStCols;
+            const int64_t c = cs + (int64_t)s * kStCols + 2 * lane;
+            if (c >= diagEnd && c < n) {
+                colpart[c] = a.x;
+                dotp += ((double)sx[2 * lane] + (double)sx[kStCols + 2 * lane]) * (double)a.x;
+            }
+            if (c + 1 >= diagEnd && c + 1 < n) {
+                colpart[c + 1] = a.y;
+                dotp += ((double)sx[2 * lane + 1] + (double)sx[kStCols + 2 * lane + 1]) * (double)a.y;
+            }
+        };
+        int issued = 0, done = 0;
+        bool ok = true;
+        for (int s = 0; s < nst; ++s) {
+            const int slot = s % kStages, round = s / kStages;
+            if (round > 0) {
+                if (!mbar_wait(&empty[slot], (round - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                finish(s - kStages);
+                done = s - kStages + 1;
+                __syncwarp();
+            }
+            const int64_t c0 = cs + (int64_t)s * kStCols;
+            const unsigned rb = (unsigned)kStCols * 4u;                 // x parts of the tile
+            const unsigned tb = (unsigned)rows * rb;                     // the tile
+            float* dst = stg + slot * kStageFloats;
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&full[slot], tb + 2 * rb);
+                bulk_g2s(dst, vb + (c0 - row0) / kStCols * (int64_t)rows * kStCols, tb, &full[slot]);
+                bulk_g2s(dst + kSymRows * kStCols, xh + c0, rb, &full[slot]);
+                bulk_g2s(dst + kSymRows * kStCols + kStCols, xl + c0, rb, &full[slot]);
+            }
+            __syncwarp();
+            issued = s + 1;
+        }
+        for (int s = done; ok && s < issued; ++s) {
+            if (!mbar_wait(&empty[s % kStages], (s / kStages) & 1)) {
+                ok = false;
+                break;
+            }
+            finish(s);
+        }
+        if (!ok) {
+            if (lane == 0) set_timeout(S, ps);
+            // the copies this CTA has in flight land before it ends
+            for (int s = max(0, issued - kStages); s < issued; ++s) mbar_wait(&full[s % kStages], (s / kStages) & 1);
+        }
+    } else {
+        float xrh[16], xrl[16], racc[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int r = warp + 8 * k;
+            xrh[k] = r < rows ? xh[row0 + r] : 0.0f;
+            xrl[k] = r < rows ? xl[row0 + r] : 0.0f;
+            racc[k] = 0.0f;
+        }
+        bool ok = true;
+        for (int s = 0; s < nst; ++s) {
+            const int slot = s % kStages;
+            if (!mbar_wait(&full[slot], (s / kStages) & 1)) {
+                ok = false;
+                break;
+            }
+            const float* sv = stg + slot * kStageFloats;
+            const float2 h = *reinterpret_cast<const float2*>(sv + kSymRows * kStCols + 2 * lane);
+            const float2 l = *reinterpret_cast<const float2*>(sv + kSymRows * kStCols + kStCols + 2 * lane);
+            // four interleaved column accumulators (rows k mod 4) keep the
+            // dependent FMA chains short
+            float ca[4][2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ca[q][0] = ca[q][1] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                if (warp + 8 * k < rows) {           // warp-uniform
+                    const float2 v = *reinterpret_cast<const float2*>(sv + (warp + 8 * k) * kStCols + 2 * lane);
+                    racc[k] = fmaf(v.x, h.x, fmaf(v.y, h.y, fmaf(v.x, l.x, fmaf(v.y, l.y, racc[k]))));
+                    ca[k & 3][0] = fmaf(v.x, xrh[k], fmaf(v.x, xrl[k], ca[k & 3][0]));
+                    ca[k & 3][1] = fmaf(v.y, xrh[k], fmaf(v.y, xrl[k], ca[k & 3][1]));
+                }
+            }
+            *reinterpret_cast<float2*>(cred + (slot * 8 + warp) * kStCols + 2 * lane) =
+                make_float2((ca[0][0] + ca[1][0]) + (ca[2][0] + ca[3][0]), (ca[0][1] + ca[1][1]) + (ca[2][1] + ca[3][1]));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+        }
+        if (!ok) {
+            if (lane == 0) set_timeout(S, ps);
+        } else {
+            float* __restrict__ rowpart = S.rowpart + ((int64_t)rhs * S.nsegCap + wk.y) * n;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                float a = racc[k];
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                const int r = warp + 8 * k;
+                if (lane == 0 && r < rows) {
+                    const double q = (double)a;
+                    rowpart[row0 + r] = a;
+                    dotp += xv[row0 + r] * q;
+                }
+            }
+        }
+    }
+    if (part) {
+        const double sdot = block_reduce(dotp);
+        if (tid == 0) part[(int64_t)rhs * S.nwork + item] = sdot;
+        if (ps && draw_last_ticket(ps, (unsigned)S.nwork))
+            pcg_alpha_finish(part + (int64_t)rhs * S.nwork, S.nwork, ps);
+    }
+}
+
 __global__ void sym_reduce_kernel(SymPanels S, int64_t n, double* __restrict__ y) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = sym_q(S, n, i, 0);
 }
 
+static mlb_status tune_sym(mlb_ctx* ctx);
+
+// Partial buffers for nrhs simultaneous products of the current plan.
 mlb_status sym_reserve(mlb_ctx* ctx, int nrhs) {
     SymPanels& S = ctx->sym;
-    if (nrhs <= S.nrhs) return MLB_OK;
-    dfree(ctx->arena_asm, S.rowpart);
-    dfree(ctx->arena_asm, S.colpart);
+    if (nrhs <= S.nrhs && S.nsegMax <= S.nsegCap) return MLB_OK;
+    nrhs = std::max(nrhs, S.nrhs);
+    Arena& A = ctx->arena_asm;
+    for (void* q : {(void*)S.rowpart, (void*)S.colpart, (void*)S.xh, (void*)S.xl}) dfree(A, q);
     S.rowpart = S.colpart = nullptr;
+    S.xh = S.xl = nullptr;
     S.nrhs = 0;
     const int64_t n = ctx->nwav;
-    S.rowpart = (double*)dalloc(ctx, ctx->arena_asm, sizeof(double) * (size_t)nrhs * S.nsegMax * n);
-    S.colpart = (double*)dalloc(ctx, ctx->arena_asm, sizeof(double) * (size_t)nrhs * S.nblk * n);
-    if (!S.rowpart || !S.colpart) return fail(ctx, MLB_ENOMEM, "symmetric product partials");
+    S.xld = sym_width(n, 0);
+    S.nsegCap = S.nsegMax;
+    S.rowpart = (float*)dalloc(ctx, A, sizeof(float) * (size_t)nrhs * S.nsegCap * n);
+    S.colpart = (float*)dalloc(ctx, A, sizeof(float) * (size_t)nrhs * S.nblk * n);
+    S.xh = (float*)dalloc(ctx, A, sizeof(float) * (size_t)nrhs * S.xld);
+    S.xl = (float*)dalloc(ctx, A, sizeof(float) * (size_t)nrhs * S.xld);
+    if (!S.rowpart || !S.colpart || !S.xh || !S.xl) return fail(ctx, MLB_ENOMEM, "symmetric product partials");
+    // entries past nwav stay zero: the writers of the split vectors stop at nwav
+    MLB_CUDA(ctx, cudaMemsetAsync(S.xh, 0, sizeof(float) * (size_t)nrhs * S.xld, ctx->stream));
+    MLB_CUDA(ctx, cudaMemsetAsync(S.xl, 0, sizeof(float) * (size_t)nrhs * S.xld, ctx->stream));
     S.nrhs = nrhs;
     return MLB_OK;
+}
+
+// Work list of the product for items of `seg` columns: (block, segment),
+// heaviest first, so the last wave of CTAs is short.
+static mlb_status sym_plan(mlb_ctx* ctx, int seg) {
+    SymPanels& S = ctx->sym;
+    const int64_t n = ctx->nwav;
+    std::vector<std::pair<int64_t, int2>> items;
+    int nsegMax = 0;
+    for (int b = 0; b < S.nblk; ++b) {
+        const int64_t rows = std::min<int64_t>(kSymRows, n - (int64_t)b * kSymRows);
+        const int64_t W = sym_width(n, b);
+        const int ns = sym_nseg(n, b, seg);
+        nsegMax = std::max(nsegMax, ns);
+        for (int s = 0; s < ns; ++s) {
+            const int64_t cols = std::min<int64_t>(seg, W - (int64_t)s * seg);
+            items.push_back({-rows * cols, make_int2(b, s)});
+        }
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<int64_t, int2>& a, const std::pair<int64_t, int2>& c) { return a.first < c.first; });
+    std::vector<int2> work;
+    for (auto& it : items) work.push_back(it.second);
+    if (work.size() > max_work_items(ctx->ncell, ctx->N)) return fail(ctx, MLB_EINVAL, "symmetric work table bound");
+    Arena& A = ctx->arena_asm;
+    if (!S.work || (int)work.size() > S.nworkCap) {
+        dfree(A, S.work);
+        S.work = (int2*)dalloc(ctx, A, sizeof(int2) * work.size());
+        if (!S.work) return fail(ctx, MLB_ENOMEM, "symmetric work table");
+        S.nworkCap = (int)work.size();
+    }
+    S.nwork = (int)work.size();
+    S.seg = seg;
+    S.nsegMax = nsegMax;
+    MLB_CUDA(ctx, cudaMemcpyAsync(S.work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, ctx->stream));
+    MLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // `work` goes out of scope
+    return sym_reserve(ctx, std::max(1, S.nrhs));
 }
 
 // Packs the FP64 panels of a complete pattern (nwav > 0) into the symmetric
@@ -235,47 +505,105 @@ mlb_status build_sym(mlb_ctx* ctx) {
     if (n <= 0) return fail(ctx, MLB_EINVAL, "symmetric storage needs wavelet rows");
     S.nblk = (int)((n + kSymRows - 1) / kSymRows);
     std::vector<int64_t> off(S.nblk);
-    std::vector<std::pair<int64_t, int2>> items;
     int64_t tot = 0;
     for (int b = 0; b < S.nblk; ++b) {
-        const int64_t rows = std::min<int64_t>(kSymRows, n - (int64_t)b * kSymRows);
-        const int64_t W = sym_width(n, b);
         off[b] = tot;
-        tot += rows * W;
-        const int ns = sym_nseg(n, b);
-        S.nsegMax = std::max(S.nsegMax, ns);
-        for (int s = 0; s < ns; ++s) {
-            const int64_t cols = std::min<int64_t>(kSymSeg, W - (int64_t)s * kSymSeg);
-            items.push_back({-rows * cols, make_int2(b, s)});
-        }
+        tot += std::min<int64_t>(kSymRows, n - (int64_t)b * kSymRows) * sym_width(n, b);
     }
-    std::stable_sort(items.begin(), items.end(),
-                     [](const std::pair<int64_t, int2>& a, const std::pair<int64_t, int2>& c) { return a.first < c.first; });
-    std::vector<int2> work;
-    for (auto& it : items) work.push_back(it.second);
-    if (work.size() > max_work_items(ctx->ncell, ctx->N)) return fail(ctx, MLB_EINVAL, "symmetric work table bound");
-    S.nwork = (int)work.size();
     S.stored = tot;
     Arena& A = ctx->arena_asm;
     S.vals = (float*)dalloc(ctx, A, sizeof(float) * tot);
     S.off = (int64_t*)dalloc(ctx, A, sizeof(int64_t) * S.nblk);
-    S.work = (int2*)dalloc(ctx, A, sizeof(int2) * work.size());
-    if (!S.vals || !S.off || !S.work) return fail(ctx, MLB_ENOMEM, "symmetric storage");
+    S.err = (int*)dalloc(ctx, A, sizeof(int));
+    if (!S.vals || !S.off || !S.err) return fail(ctx, MLB_ENOMEM, "symmetric storage");
     cudaStream_t st = ctx->stream;
+    MLB_CUDA(ctx, cudaMemsetAsync(S.err, 0, sizeof(int), st));
     MLB_CUDA(ctx, cudaMemcpyAsync(S.off, off.data(), sizeof(int64_t) * S.nblk, cudaMemcpyHostToDevice, st));
-    MLB_CUDA(ctx, cudaMemcpyAsync(S.work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, st));
     const int64_t warps = std::min<int64_t>(n, (int64_t)std::max(ctx->nsm, 1) * 64);
     sym_pack_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(ctx->pan, ctx->pan.rowCell, ctx->cells.wOff,
                                                                          n, S);
     MLB_CHECK_LAUNCH(ctx, "sym_pack_kernel");
-    // the host vectors above go out of scope: wait for their copies
-    MLB_CUDA(ctx, cudaStreamSynchronize(st));
-    return sym_reserve(ctx, 1);
+    return tune_sym(ctx);   // synchronises the stream before `off` goes out of scope
 }
 
-void sym_launch(mlb_ctx* ctx, const double* x, int nrhs, double* part, PcgState* st) {
+void sym_launch(mlb_ctx* ctx, const double* x, int nrhs, double* part, PcgState* st, bool presplit) {
     const SymPanels& S = ctx->sym;
-    sym_spmv_f32_kernel<<<(unsigned)(S.nwork * nrhs), 256, 0, ctx->stream>>>(S, ctx->nwav, x, nrhs, part, st);
+    if (ctx->sym_variant == 1) {
+        if (!presplit) {
+            xsplit_kernel<<<kVecBlocks, 256, 0, ctx->stream>>>(ctx->nwav, nrhs, x, S.xld, S.xh, S.xl, st);
+            ctx->launches += 1;
+        }
+        sym_spmv_bulk_kernel<<<(unsigned)(S.nwork * nrhs), 288, kBulkSmem, ctx->stream>>>(S, ctx->nwav, x, nrhs,
+                                                                                          part, st);
+    } else {
+        sym_spmv_f32_kernel<<<(unsigned)(S.nwork * nrhs), 256, 0, ctx->stream>>>(S, ctx->nwav, x, nrhs, part, st);
+    }
+}
+
+// Chooses the form of the product (0: plain loads with L2 prefetch, 1:
+// bulk-copy pipeline) and the columns per work item (2,048, 1,024 or 512:
+// fewer, longer items against a shorter last wave) by timing every pair on
+// the context's own matrix (CUDA events on its stream, outside any capture),
+// cached per (device, size bucket) for the rest of the process.
+static std::mutex g_sym_mutex;
+static std::map<std::pair<int, int>, std::pair<int, int>> g_sym_cache;
+
+static mlb_status tune_sym(mlb_ctx* ctx) {
+    MLB_CUDA(ctx, cudaFuncSetAttribute(sym_spmv_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kBulkSmem));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int bucket = 0;
+    while ((1LL << (bucket + 1)) <= ctx->nwav) ++bucket;
+    const auto key = std::make_pair(dev, bucket);
+    {
+        std::lock_guard<std::mutex> lock(g_sym_mutex);
+        auto it = g_sym_cache.find(key);
+        if (it != g_sym_cache.end()) {
+            ctx->sym_variant = it->second.first;
+            return sym_plan(ctx, it->second.second);
+        }
+    }
+    double* u = ctx->vec + 3 * ctx->nwav;
+    MLB_CUDA(ctx, cudaMemsetAsync(u, 0, sizeof(double) * ctx->nwav, ctx->stream));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    std::pair<int, int> bestc(0, 2048);
+    mlb_status s = MLB_OK;
+    for (int seg : {2048, 1024, 512}) {
+        if ((s = sym_plan(ctx, seg)) != MLB_OK) break;
+        for (int v = 0; v < 2; ++v) {
+            ctx->sym_variant = v;
+            sym_launch(ctx, u, 1, nullptr, nullptr);
+            cudaEventRecord(e0, ctx->stream);
+            for (int k = 0; k < 3; ++k) sym_launch(ctx, u, 1, nullptr, nullptr);
+            cudaEventRecord(e1, ctx->stream);
+            ctx->launches += 4;
+            const cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                s = cuda_fail(ctx, e, "symmetric product tuning");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bestc = std::make_pair(v, seg);
+            }
+        }
+        if (s != MLB_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != MLB_OK) return s;
+    {
+        std::lock_guard<std::mutex> lock(g_sym_mutex);
+        g_sym_cache[key] = bestc;
+    }
+    ctx->sym_variant = bestc.first;
+    return sym_plan(ctx, bestc.second);
 }
 
 void sym_reduce(mlb_ctx* ctx, double* out) {

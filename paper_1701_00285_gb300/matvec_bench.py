@@ -27,6 +27,8 @@ def main(argv=None) -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--leaf-size", type=int, default=None, help="default: the workload's leaf size")
     ap.add_argument("--matrix-free", action="store_true", help="d = 10 three-step product")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="symmetric FP32 product form (0 loads, 1 bulk copies); default: the autotuned one")
     a = ap.parse_args(argv)
 
     import torch
@@ -42,6 +44,8 @@ def main(argv=None) -> None:
             c.set_stream(st.cuda_stream)
             c.build_basis(P.points, P.w)
             c.assemble(P.nu, P.rho, P.nugget, math.inf)
+            if a.variant is not None and prec == "mixed" and not a.matrix_free:
+                c.set_product_variant(a.variant)
             nw = c.nwav
             with torch.cuda.stream(st):
                 u = torch.randn(nw, dtype=torch.float64, device="cuda",
@@ -73,7 +77,8 @@ def main(argv=None) -> None:
                 nnz = inf["nnz_unique"] if inf["symmetric"] else nw * nw
                 algo = nnz * vb + 2 * nw * 8
                 print(json.dumps({"precision": prec, "n": a.n, "nwav": nw, "nnz": nnz,
-                                  "symmetric": inf["symmetric"], "stored_values": inf["product_values"],
+                                  "symmetric": inf["symmetric"], "variant": inf["product_variant"],
+                                  "stored_values": inf["product_values"],
                                   "ms": ms, "algorithmic_bytes": algo, "GBps": algo / ms / 1e6}), flush=True)
         finally:
             c.close()

@@ -82,12 +82,15 @@ def test_cw_product_large_matches_oracle_elementwise(pkg, mid_problem, prec, tol
     ctx.assemble(P.nu, P.rho, P.nugget, math.inf)
     assert ctx.nwav % 128 != 0               # ragged last row block of the symmetric storage
     v = np.random.default_rng(21).standard_normal(P.N)
-    got = ctx.apply_Wt(ctx.cw_matvec(ctx.apply_W(v)))
-    ctx.close()
     ref = projected_cov(P, v)
     scale = np.abs(ref).max()
-    assert np.abs(got - ref).max() < tol * scale
-    assert rel(got, ref) < tol
+    for variant in ((0, 1) if prec == "mixed" else (None,)):
+        if variant is not None:
+            ctx.set_product_variant(variant)
+        got = ctx.apply_Wt(ctx.cw_matvec(ctx.apply_W(v)))
+        assert np.abs(got - ref).max() < tol * scale
+        assert rel(got, ref) < tol
+    ctx.close()
 
 
 @pytest.mark.parametrize("seed,N,d,w,n0", [(31, 700, 2, 1, 32), (32, 1000, 3, 1, 64), (33, 2200, 5, 1, 64),
@@ -105,9 +108,15 @@ def test_symmetric_product_matches_oracle(pkg, seed, N, d, w, n0):
         got = ctx.apply_Wt(ctx.cw_matvec(ctx.apply_W(v)))
         ref = projected_cov(P, v)
         assert np.abs(got - ref).max() < 1e-6 * np.abs(ref).max()
-    # the same product twice gives the same bits (fixed summation order)
+    # the same product twice gives the same bits (fixed summation order); the
+    # two forms (plain loads, bulk-copy pipeline) agree to FP32 rounding
     u = rng.standard_normal(ctx.nwav)
-    assert np.array_equal(ctx.cw_matvec(u), ctx.cw_matvec(u))
+    outs = []
+    for v in (0, 1):
+        ctx.set_product_variant(v)
+        outs.append(ctx.cw_matvec(u))
+        assert np.array_equal(outs[-1], ctx.cw_matvec(u))
+    assert np.abs(outs[0] - outs[1]).max() <= 1e-6 * np.abs(outs[0]).max()
     ctx.close()
 
 
