@@ -183,59 +183,101 @@ def describe(P) -> str:
             f"tau={tau}, PCG tol {P.pcg_rtol:g}, {P.targets.shape[0]} targets")
 
 
-def _oracle_sample(name: str, sample_n: int, sample_m: int, n: int, m: int) -> float:
-    """Seconds the oracle takes for one multilevel BLUP on the subsample."""
+ORACLE_SIZES = (512, 1024, 2048)
+
+
+def _oracle_worker(name: str, sizes, seed: int, n: int, m: int):
+    """One single-threaded oracle process: the multilevel BLUP (Alg. 7
+    assembly, PCG, trend step, prediction) on a seeded subsample of the
+    workload at each size, targets in the workload's proportion.  Returns
+    [(size, seconds, PCG iterations)]."""
     import workloads as wl
     from oracle import mlblup
     P = getattr(wl, name)(N=n, M=m)
-    S = wl.subsample(P, sample_n, seed=1, m=sample_m)
-    t0 = time.perf_counter()
-    mlblup.blup(S.points, S.Z, S.targets, S.w, S.nu, S.rho, S.nugget, S.leaf_size,
-                tau_factor=S.tau_factor, rtol=S.pcg_rtol, maxit=20000)
-    return time.perf_counter() - t0
+    out = []
+    for s in sizes:
+        S = wl.subsample(P, s, seed=seed, m=max(1, s * m // n))
+        t0 = time.perf_counter()
+        r = mlblup.blup(S.points, S.Z, S.targets, S.w, S.nu, S.rho, S.nugget, S.leaf_size,
+                        tau_factor=S.tau_factor, rtol=S.pcg_rtol, maxit=20000)
+        out.append((s, time.perf_counter() - t0, int(r["info"].get("iterations", 0))))
+    return out
 
 
-def cpu_baseline(P, sample_n=2048, sample_m=512):
-    """The oracle as it stands (numpy FP64: Alg. 7 assembly, PCG, trend step,
-    prediction) on a seeded subsample of the same workload, in a fresh
-    single-threaded process, extrapolated to the full size by the N^2 cost of
-    kernel evaluation."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import bench, sys; print(bench._oracle_sample(%r, %d, %d, %d, %d))"
-            % (P.meta["generator"], sample_n, sample_m, P.N, P.targets.shape[0]))
-    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    dt = float(r.stdout.strip().splitlines()[-1])
-    scale = (P.N / sample_n) ** 2
-    return {"value": 1.0 / (dt * scale), "unit": "BLUP solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle multilevel BLUP (Alg. 7 assembly, PCG, trend, prediction) on a seeded "
-                      f"{sample_n}-point subsample with {sample_m} targets, one thread: {dt:.2f} s; "
-                      f"scaled to N={P.N} by (N/{sample_n})^2 = {scale:.0f}x",
-            "sample_seconds": dt}
+def fit_power_law(sizes, seconds):
+    """Least-squares fit of log t = log a + k log n; returns (a, k)."""
+    x = np.log(np.asarray(sizes, dtype=np.float64))
+    y = np.log(np.asarray(seconds, dtype=np.float64))
+    k, la = np.polyfit(x, y, 1)
+    return float(math.exp(la)), float(k)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(P, sizes=ORACLE_SIZES, workers=None):
+    """The oracle as it stands (numpy FP64), timed on every host core: one
+    single-threaded process per core (a spawned pool, safe beside an
+    initialised CUDA context), all running the same seeded subsamples of the
+    workload at once.  The per-size medians are fitted with t = a n^k and the
+    fit gives the time of one full-size solve on one loaded core; the cores
+    together finish `cores` such solves in that time."""
+    import multiprocessing as mp
+    C = workers or host_cores()
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(C) as pool:
+            res = pool.starmap(_oracle_worker, [(P.meta["generator"], tuple(sizes), 1 + k, P.N, P.targets.shape[0])
+                                                for k in range(C)])
+        wall = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    med = [float(np.median([r[i][1] for r in res])) for i in range(len(sizes))]
+    its = [int(np.median([r[i][2] for r in res])) for i in range(len(sizes))]
+    a, k = fit_power_law(sizes, med)
+    t_full = a * P.N ** k
+    value = C / t_full
+    return {"value": value, "unit": "BLUP solves/s", "cores": C, "kind": "oracle",
+            "sample": (f"oracle multilevel BLUP (Alg. 7 assembly, PCG, trend, prediction) on seeded subsamples "
+                       f"n = {', '.join(str(s) for s in sizes)} (targets in the workload's proportion), one "
+                       f"single-threaded process per host core ({C} at once, {wall:.1f} s wall); median seconds "
+                       f"{', '.join(f'{t:.2f}' for t in med)}, PCG iterations {', '.join(str(i) for i in its)}; "
+                       f"fit t = {a:.3g} n^{k:.2f} gives {t_full:.0f} s per N={P.N} solve per core"),
+            "sizes": list(sizes), "seconds": med, "iterations": its, "exponent": k,
+            "seconds_full_size_per_core": t_full, "wall_seconds": wall}
 
 
 # ------------------------------------------------------------ reference -----
 def run_reference(args, rank, world):
+    """The oracle arm: every step is one cpu_baseline measurement (all host
+    cores, the same procedure as the cpu_baseline key of the GPU arm); the
+    value is the median over the timed steps."""
     if rank != 0:
         return
     P = workload(args)
     for _ in range(max(0, args.warmup)):
-        cpu_baseline(P, sample_n=256, sample_m=64)
-    vals = []
-    t_total = 0.0
-    for _ in range(args.steps):
-        cb = cpu_baseline(P, sample_n=1024, sample_m=256)
-        vals.append(cb["value"])
-        t_total += cb["sample_seconds"]
-    value = args.steps / sum(1.0 / v for v in vals)
+        cpu_baseline(P, sizes=ORACLE_SIZES[:1])
+    runs = [cpu_baseline(P) for _ in range(args.steps)]
+    value = float(np.median([r["value"] for r in runs]))
+    cb = runs[-1]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "BLUP solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1000.0 * cb["cores"] / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": describe(P), "cache": "oracle on host cores"},
-            "cpu_baseline": {"value": value, "unit": "BLUP solves/s", "cores": 1,
-                             "kind": "oracle", "sample": cb["sample"]},
+            "cpu_baseline": {"value": value, "unit": "BLUP solves/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"], "exponent": cb["exponent"]},
             "e2e": {"value": value, "unit": "BLUP solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -541,7 +583,8 @@ def run_ours(args, rank, world, local_rank):
             "speedup": (head["value"] / other["value"]) if args.precision == "mixed" else (other["value"] / head["value"])}
         other["ctx"].close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(P).items() if k != "sample_seconds"}
+        cb = cpu_baseline(P)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "exponent")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     head["ctx"].close()

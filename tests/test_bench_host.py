@@ -46,3 +46,23 @@ def test_describe_names_the_workload_and_its_sizes():
     s = bench.describe(P)
     assert s.startswith("heldout_5d_n1024") and "d=5" in s and "16 targets" in s
     assert "tau=inf" in s and math.isinf(P.tau_factor)
+
+
+def test_power_law_fit_recovers_exponent():
+    sizes = [512, 1024, 2048, 4096]
+    a, k = bench.fit_power_law(sizes, [3e-9 * n ** 2.6 for n in sizes])
+    assert abs(k - 2.6) < 1e-12 and abs(a / 3e-9 - 1) < 1e-9
+
+
+def test_cpu_baseline_pool_on_a_tiny_sample():
+    """Two single-threaded oracle processes on tiny subsamples: the result
+    carries the cores used, the per-size medians and iterations, and the
+    throughput the fit implies for the full workload."""
+    P = wl.heldout_5d(N=4096, M=64)
+    P.meta["generator"] = "heldout_5d"
+    r = bench.cpu_baseline(P, sizes=(128, 256, 384), workers=2)
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["unit"] == "BLUP solves/s"
+    assert len(r["seconds"]) == 3 and all(t > 0 for t in r["seconds"])
+    assert all(i > 0 for i in r["iterations"])
+    a, k = bench.fit_power_law(r["sizes"], r["seconds"])
+    assert math.isclose(r["value"], 2 / (a * 4096 ** k), rel_tol=1e-12)
