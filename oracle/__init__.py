@@ -7,8 +7,11 @@ sides use is ``workloads`` (seeded input generators, no method arithmetic).
 
 What it computes, in the paper's order and notation:
 
-* ``matern``   -- the Matern covariance (Def. "Matern covariance function") for
-                  half-integer smoothness, and its derivative in log(rho).
+* ``matern``   -- the Matern covariance (Def. "Matern covariance function"):
+                  closed forms at nu = 1/2, 3/2, 5/2, the definition with the
+                  library K_nu for any other nu; the Gaussian kernel of the
+                  accuracy study (Sec. 8.2); the anisotropic distance r(theta)
+                  (Sec. 3); derivatives in log(rho).
 * ``design``   -- the total-degree monomial design matrix X (Sec. 2, Q^d_w).
 * ``tree``     -- the kd-tree (Algorithms 1-3: Rule, InitialTree, MakeTree).
 * ``basis``    -- the multilevel basis W, L (Sec. 3.1, steps 1-5 and the

@@ -19,23 +19,23 @@ from .pattern import pattern as make_pattern
 
 
 def cell_cov(basis: Basis, points: np.ndarray, li: int, m: int, lj: int, q: int,
-             nu: float, rho: float, nugget: float) -> np.ndarray:
+             nu: float, rho: float, nugget: float, **kf) -> np.ndarray:
     im, iq = basis.cell_points(li, m), basis.cell_points(lj, q)
-    C = kernel_matrix(points[im], points[iq], nu, rho)
+    C = kernel_matrix(points[im], points[iq], nu, rho, **kf)
     if nugget:
         same = im[:, None] == iq[None, :]
         C = C + nugget * same
     return C
 
 
-def block(basis: Basis, points, li, m, lj, q, nu, rho, nugget) -> np.ndarray:
+def block(basis: Basis, points, li, m, lj, q, nu, rho, nugget, **kf) -> np.ndarray:
     """Psi_m^T C(S_m, S_q) Psi_q for cell m of level li and q of level lj."""
-    C = cell_cov(basis, points, li, m, lj, q, nu, rho, nugget)
+    C = cell_cov(basis, points, li, m, lj, q, nu, rho, nugget, **kf)
     return basis.psi[li][m].T @ C @ basis.psi[lj][q]
 
 
 def assemble(basis: Basis, points: np.ndarray, nu: float, rho: float, nugget: float,
-             tau_factor: float, pat=None) -> dict:
+             tau_factor: float, pat=None, **kf) -> dict:
     """Algorithm 7 over all level pairs.  Returns {(li, m, lj, q): block} holding
     both (m, q) and the mirrored (q, m) entries, plus the pattern."""
     if pat is None:
@@ -50,7 +50,7 @@ def assemble(basis: Basis, points: np.ndarray, nu: float, rho: float, nugget: fl
                     continue
                 if i == j and q < m:
                     continue
-                B = block(basis, points, i, m, j, int(q), nu, rho, nugget)
+                B = block(basis, points, i, m, j, int(q), nu, rho, nugget, **kf)
                 blocks[(i, m, j, int(q))] = B
                 if (i, m) != (j, int(q)):
                     blocks[(j, int(q), i, m)] = B.T

@@ -18,26 +18,27 @@ from .design import box, design_matrix
 from .matern import covariance, kernel_matrix
 
 
-def dense_blup(points, Z, targets, w, nu, rho, nugget):
+def dense_blup(points, Z, targets, w, nu, rho, nugget, **kf):
+    """kf: covariance family and axis weights (matern.kernel_matrix)."""
     lo, hi = box(points)
     X = design_matrix(points, w, lo, hi)
-    C = covariance(points, nu, rho, nugget)
+    C = covariance(points, nu, rho, nugget, **kf)
     cf = cho_factor(C, lower=True)
     CiX = cho_solve(cf, X)
     CiZ = cho_solve(cf, Z)
     beta = np.linalg.solve(X.T @ CiX, X.T @ CiZ)
     gamma = cho_solve(cf, Z - X @ beta)
     K0 = design_matrix(targets, w, lo, hi)
-    c0 = kernel_matrix(targets, points, nu, rho)
+    c0 = kernel_matrix(targets, points, nu, rho, **kf)
     yhat = K0 @ beta + c0 @ gamma
     return {"beta": beta, "gamma": gamma, "yhat": yhat, "X": X, "C": C}
 
 
-def saddle_point_solve(points, Z, w, nu, rho, nugget):
+def saddle_point_solve(points, Z, w, nu, rho, nugget, **kf):
     """Direct solve of [[C, X], [X^T, 0]] [gamma; beta] = [Z; 0]."""
     lo, hi = box(points)
     X = design_matrix(points, w, lo, hi)
-    C = covariance(points, nu, rho, nugget)
+    C = covariance(points, nu, rho, nugget, **kf)
     N, p = X.shape
     K = np.zeros((N + p, N + p))
     K[:N, :N] = C
@@ -47,13 +48,13 @@ def saddle_point_solve(points, Z, w, nu, rho, nugget):
     return sol[:N], sol[N:]
 
 
-def mse_at(points, targets, w, nu, rho, nugget):
+def mse_at(points, targets, w, nu, rho, nugget, **kf):
     """Kriging mean squared error at targets (Sec. 5.2, after eq. Spatial)."""
     lo, hi = box(points)
     X = design_matrix(points, w, lo, hi)
-    C = covariance(points, nu, rho, nugget)
+    C = covariance(points, nu, rho, nugget, **kf)
     cf = cho_factor(C, lower=True)
-    c0 = kernel_matrix(points, targets, nu, rho)
+    c0 = kernel_matrix(points, targets, nu, rho, **kf)
     Cic = cho_solve(cf, c0)
     A = X.T @ cho_solve(cf, X)
     K0 = design_matrix(targets, w, lo, hi)

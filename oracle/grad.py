@@ -32,21 +32,22 @@ from .matern import covariance, dmatern_dlogrho, distances, kernel_matrix
 from .pcg import pcg
 
 
-def loss_dense(points, Z, targets, y, w, nu, rho, nugget):
+def loss_dense(points, Z, targets, y, w, nu, rho, nugget, **kf):
     from .dense import dense_blup
-    r = dense_blup(points, Z, targets, w, nu, rho, nugget)
+    r = dense_blup(points, Z, targets, w, nu, rho, nugget, **kf)
     return float(np.mean((r["yhat"] - y) ** 2))
 
 
-def grad_dense(points, Z, targets, y, w, nu, rho, nugget):
+def grad_dense(points, Z, targets, y, w, nu, rho, nugget, family="matern", axis=None):
+    kf = {"family": family, "axis": axis}
     lo, hi = box(points)
     X = design_matrix(points, w, lo, hi)
-    C = covariance(points, nu, rho, nugget)
+    C = covariance(points, nu, rho, nugget, **kf)
     cf = cho_factor(C, lower=True)
     CiX = cho_solve(cf, X)
     beta = np.linalg.solve(X.T @ CiX, X.T @ cho_solve(cf, Z))
     gamma = cho_solve(cf, Z - X @ beta)
-    c0 = kernel_matrix(targets, points, nu, rho)
+    c0 = kernel_matrix(targets, points, nu, rho, **kf)
     K0 = design_matrix(targets, w, lo, hi)
     yhat = c0 @ gamma + K0 @ beta
     M = targets.shape[0]
@@ -55,8 +56,8 @@ def grad_dense(points, Z, targets, y, w, nu, rho, nugget):
     a, b = c0.T @ g, K0.T @ g
     mu = np.linalg.solve(X.T @ CiX, X.T @ cho_solve(cf, a) - b)
     lam = cho_solve(cf, a - X @ mu)
-    dC = dmatern_dlogrho(distances(points, points), nu, rho)
-    dc0 = dmatern_dlogrho(distances(targets, points), nu, rho)
+    dC = dmatern_dlogrho(distances(points, points, axis), nu, rho, family)
+    dc0 = dmatern_dlogrho(distances(targets, points, axis), nu, rho, family)
     d_logrho = g @ (dc0 @ gamma) - lam @ (dC @ gamma)
     d_lognug = -nugget * (lam @ gamma)
     return loss, float(d_logrho), float(d_lognug)

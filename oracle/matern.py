@@ -14,12 +14,20 @@ with s = sqrt(2 nu) r / rho,
 
 Unit variance: phi(0) = 1.  The covariance matrix of the observations adds
 the nugget eta on its diagonal (C <- C + eta I on data points only).
+
+Any other smoothness nu > 0 is the definition itself, with the library's
+modified Bessel function K_nu (scipy.special.kv) as one step.  The same
+module gives the Gaussian kernel of the accuracy study (Sec. 8.2),
+phi(r) = exp(-r^2 / (2 theta^2)) with theta passed as ``rho``, and the
+anisotropic distance of Sec. 3, r(theta)^2 = (x - y)^T diag(theta) (x - y),
+with the axis weights theta_k passed as ``axis`` (None: Euclidean).
 """
 from __future__ import annotations
 
 import math
 
 import numpy as np
+from scipy.special import gammaln as _gammaln, kv as _kv
 
 SUPPORTED_NU = (0.5, 1.5, 2.5)
 
@@ -28,8 +36,41 @@ def _s(r, nu, rho):
     return math.sqrt(2.0 * nu) * np.asarray(r, dtype=np.float64) / rho
 
 
-def matern(r, nu: float, rho: float) -> np.ndarray:
-    """phi(r; nu, rho) for nu in {1/2, 3/2, 5/2} (unit variance)."""
+def matern_kv(s, nu: float) -> np.ndarray:
+    """The definition with the library's K_nu: phi = (s^nu K_nu(s)) / (Gamma(nu)
+    2^(nu-1)) at s = sqrt(2 nu) r / rho, and phi(0) = 1 (the limit of s^nu
+    K_nu(s) as s -> 0 is Gamma(nu) 2^(nu-1))."""
+    s = np.asarray(s, dtype=np.float64)
+    out = np.ones_like(s)
+    pos = s > 0
+    sp = s[pos]
+    # in logarithms, so that Gamma(nu) 2^(nu-1) and s^nu K_nu(s) stay in range
+    with np.errstate(divide="ignore"):
+        out[pos] = np.exp(nu * np.log(sp) + np.log(_kv(nu, sp)) - _gammaln(nu) - (nu - 1.0) * math.log(2.0))
+    return out
+
+
+def dmatern_kv(s, nu: float) -> np.ndarray:
+    """-s phi'(s) from the definition: d/ds [s^nu K_nu(s)] = -s^nu K_{nu-1}(s)
+    (A&S 9.6.28), so -s phi'(s) = s^(nu+1) K_{nu-1}(s) / (Gamma(nu) 2^(nu-1))."""
+    s = np.asarray(s, dtype=np.float64)
+    out = np.zeros_like(s)
+    pos = s > 0
+    sp = s[pos]
+    with np.errstate(divide="ignore"):
+        out[pos] = np.exp((nu + 1.0) * np.log(sp) + np.log(_kv(nu - 1.0, sp)) - _gammaln(nu)
+                          - (nu - 1.0) * math.log(2.0))
+    return out
+
+
+def matern(r, nu: float, rho: float, family: str = "matern") -> np.ndarray:
+    """phi(r; nu, rho) (unit variance): closed forms at nu = 1/2, 3/2, 5/2, the
+    definition with K_nu otherwise; family="gaussian": exp(-r^2 / (2 rho^2))."""
+    if family == "gaussian":
+        t = np.asarray(r, dtype=np.float64) / rho
+        return np.exp(-0.5 * t * t)
+    if family != "matern":
+        raise ValueError(f"unknown covariance family {family!r}")
     s = _s(r, nu, rho)
     e = np.exp(-s)
     if nu == 0.5:
@@ -38,17 +79,24 @@ def matern(r, nu: float, rho: float) -> np.ndarray:
         return (1.0 + s) * e
     if nu == 2.5:
         return (1.0 + s + s * s / 3.0) * e
-    raise ValueError(f"nu={nu} not supported (half-integer 1/2, 3/2, 5/2 only)")
+    if not nu > 0:
+        raise ValueError(f"nu={nu} must be positive")
+    return matern_kv(s, nu)
 
 
-def dmatern_dlogrho(r, nu: float, rho: float) -> np.ndarray:
+def dmatern_dlogrho(r, nu: float, rho: float, family: str = "matern") -> np.ndarray:
     """d phi / d log(rho).  Since s is proportional to 1/rho, ds/dlog(rho) = -s,
     so the derivative is -s phi'(s):
 
         nu = 1/2 : s e^{-s}
         nu = 3/2 : s^2 e^{-s}
         nu = 5/2 : (s^2/3)(1 + s) e^{-s}
+        other nu : s^(nu+1) K_{nu-1}(s) / (Gamma(nu) 2^(nu-1))
+        Gaussian : (r/rho)^2 exp(-r^2 / (2 rho^2))
     """
+    if family == "gaussian":
+        t = np.asarray(r, dtype=np.float64) / rho
+        return t * t * np.exp(-0.5 * t * t)
     s = _s(r, nu, rho)
     e = np.exp(-s)
     if nu == 0.5:
@@ -57,35 +105,38 @@ def dmatern_dlogrho(r, nu: float, rho: float) -> np.ndarray:
         return s * s * e
     if nu == 2.5:
         return (s * s / 3.0) * (1.0 + s) * e
-    raise ValueError(f"nu={nu} not supported")
+    return dmatern_kv(s, nu)
 
 
-def distances(x: np.ndarray, y: np.ndarray) -> np.ndarray:
-    """Euclidean distances between rows of x (m,d) and y (n,d), formed from the
-    coordinate differences (not from |x|^2 + |y|^2 - 2 x.y)."""
+def distances(x: np.ndarray, y: np.ndarray, axis=None) -> np.ndarray:
+    """Distances between rows of x (m,d) and y (n,d), formed from the coordinate
+    differences (not from |x|^2 + |y|^2 - 2 x.y).  With axis weights theta_k
+    (Sec. 3): r^2 = sum_k theta_k (x_k - y_k)^2; None: Euclidean."""
     acc = np.zeros((x.shape[0], y.shape[0]))
     for k in range(x.shape[1]):
         diff = x[:, k][:, None] - y[:, k][None, :]
-        acc += diff * diff
+        acc += diff * diff if axis is None else axis[k] * (diff * diff)
     return np.sqrt(acc)
 
 
-def kernel_matrix(x: np.ndarray, y: np.ndarray, nu: float, rho: float) -> np.ndarray:
-    """[phi(|x_i - y_j|)]_{ij} (no nugget)."""
-    return matern(distances(x, y), nu, rho)
+def kernel_matrix(x: np.ndarray, y: np.ndarray, nu: float, rho: float, family: str = "matern",
+                  axis=None) -> np.ndarray:
+    """[phi(r(x_i, y_j))]_{ij} (no nugget)."""
+    return matern(distances(x, y, axis), nu, rho, family)
 
 
 def kernel_matvec(x: np.ndarray, y: np.ndarray, v: np.ndarray, nu: float, rho: float,
-                  chunk: int = 2048) -> np.ndarray:
-    """sum_j phi(|x_i - y_j|) v_j, in row chunks (no nugget)."""
+                  chunk: int = 2048, family: str = "matern", axis=None) -> np.ndarray:
+    """sum_j phi(r(x_i, y_j)) v_j, in row chunks (no nugget)."""
     out = np.empty(x.shape[0])
     for s in range(0, x.shape[0], chunk):
-        out[s:s + chunk] = kernel_matrix(x[s:s + chunk], y, nu, rho) @ v
+        out[s:s + chunk] = kernel_matrix(x[s:s + chunk], y, nu, rho, family, axis) @ v
     return out
 
 
-def covariance(x: np.ndarray, nu: float, rho: float, nugget: float) -> np.ndarray:
-    """Covariance matrix C of the observations at x: phi(|x_i - x_j|) + eta delta_ij."""
-    c = kernel_matrix(x, x, nu, rho)
+def covariance(x: np.ndarray, nu: float, rho: float, nugget: float, family: str = "matern",
+               axis=None) -> np.ndarray:
+    """Covariance matrix C of the observations at x: phi(r(x_i, x_j)) + eta delta_ij."""
+    c = kernel_matrix(x, x, nu, rho, family, axis)
     c[np.diag_indices_from(c)] += nugget
     return c

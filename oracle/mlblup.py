@@ -23,9 +23,9 @@ from .pcg import pcg
 from .tree import build_tree
 
 
-def cov_matvec(points, v, nu, rho, nugget):
-    """C v with C = [phi(|x_i - x_j|)] + eta I."""
-    return kernel_matvec(points, points, v, nu, rho) + nugget * v
+def cov_matvec(points, v, nu, rho, nugget, **kf):
+    """C v with C = [phi(r(x_i, x_j))] + eta I (kf: covariance family, axis weights)."""
+    return kernel_matvec(points, points, v, nu, rho, **kf) + nugget * v
 
 
 def setup(points, w, leaf_size, rank_rtol=None):
@@ -34,19 +34,19 @@ def setup(points, w, leaf_size, rank_rtol=None):
 
 
 def solve(basis, points, Z, nu, rho, nugget, tau_factor, rtol=1e-10, maxit=10000,
-          precond=True, matvec="assembled", exact=False, asm=None):
+          precond=True, matvec="assembled", exact=False, asm=None, **kf):
     ZW = basis.apply_W(Z)
     info = {}
     if matvec == "assembled":
         if asm is None:
-            asm = assemble(basis, points, nu, rho, nugget, tau_factor)
+            asm = assemble(basis, points, nu, rho, nugget, tau_factor, **kf)
         A = to_sparse(basis, asm)
         info["nnz"] = A.nnz
         info["asm"] = asm
         mv = lambda v: A @ v
         diag = A.diagonal()
     else:
-        mv = lambda v: basis.apply_W(cov_matvec(points, basis.apply_Wt(v), nu, rho, nugget))
+        mv = lambda v: basis.apply_W(cov_matvec(points, basis.apply_Wt(v), nu, rho, nugget, **kf))
         diag = None
         A = None
     if exact:
@@ -61,23 +61,23 @@ def solve(basis, points, Z, nu, rho, nugget, tau_factor, rtol=1e-10, maxit=10000
                     converged=res.converged, breakdown=res.breakdown)
     gamma = basis.apply_Wt(gW)
     X = basis.X
-    r = Z - cov_matvec(points, gamma, nu, rho, nugget)
+    r = Z - cov_matvec(points, gamma, nu, rho, nugget, **kf)
     beta = np.linalg.solve(X.T @ X, X.T @ r)
     info["ZW"] = ZW
     info["gW"] = gW
     return gamma, beta, info
 
 
-def predict(basis, points, gamma, beta, targets, nu, rho):
+def predict(basis, points, gamma, beta, targets, nu, rho, **kf):
     """Eq. Spatial: k(x0)^T beta-hat + c(x0)^T gamma-hat (no nugget in c)."""
     K0 = design_matrix(targets, basis.w, basis.lo, basis.hi)
-    return K0 @ beta + kernel_matvec(targets, points, gamma, nu, rho)
+    return K0 @ beta + kernel_matvec(targets, points, gamma, nu, rho, **kf)
 
 
 def blup(points, Z, targets, w, nu, rho, nugget, leaf_size, tau_factor=math.inf,
-         rtol=1e-10, maxit=10000, precond=True, matvec="assembled", exact=False):
+         rtol=1e-10, maxit=10000, precond=True, matvec="assembled", exact=False, **kf):
     basis = setup(points, w, leaf_size)
     gamma, beta, info = solve(basis, points, Z, nu, rho, nugget, tau_factor, rtol, maxit,
-                              precond, matvec, exact)
-    yhat = predict(basis, points, gamma, beta, targets, nu, rho)
+                              precond, matvec, exact, **kf)
+    yhat = predict(basis, points, gamma, beta, targets, nu, rho, **kf)
     return {"basis": basis, "gamma": gamma, "beta": beta, "yhat": yhat, "info": info}

@@ -44,9 +44,74 @@ def test_dlogrho_matches_central_difference(nu):
     np.testing.assert_allclose(matern.dmatern_dlogrho(r, nu, rho), fd, rtol=1e-8, atol=1e-11)
 
 
-def test_unsupported_nu_raises():
+def test_nonpositive_nu_and_unknown_family_raise():
     with pytest.raises(ValueError):
-        matern.matern(np.array([1.0]), 0.75, 1.0)
+        matern.matern(np.array([1.0]), -0.5, 1.0)
+    with pytest.raises(ValueError):
+        matern.matern(np.array([1.0]), 1.5, 1.0, family="cauchy")
+
+
+GENERAL_NU = [0.3, 0.75, 1.0, 1.25, 3.7]
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+def test_general_nu_path_matches_closed_forms(nu):
+    """The K_nu form of the definition (used for every other nu) reproduces the
+    half-integer closed forms: pins its constant 1 / (Gamma(nu) 2^(nu-1)) and
+    its argument s = sqrt(2 nu) r / rho."""
+    r = np.concatenate([[0.0], np.logspace(-5, 1.2, 120)])
+    s = math.sqrt(2 * nu) * r / 0.4
+    np.testing.assert_allclose(matern.matern_kv(s, nu), matern.matern(r, nu, 0.4), rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(matern.dmatern_kv(s, nu), matern.dmatern_dlogrho(r, nu, 0.4), rtol=1e-11,
+                               atol=1e-300)
+
+
+@pytest.mark.parametrize("nu", GENERAL_NU)
+def test_general_nu_matches_integral_representation(nu):
+    """K_nu(s) = int_0^inf exp(-s cosh t) cosh(nu t) dt (A&S 9.6.24), by
+    adaptive quadrature: independent of the library's K_nu."""
+    from scipy.integrate import quad
+    for s in (1e-3, 0.05, 0.5, 1.0, 2.0, 5.0, 12.0):
+        # past t_max the integrand is below exp(-80) of its peak
+        t_max = math.acosh(1.0 + 80.0 / s) + 1.0
+        K, _ = quad(lambda t: math.exp(-s * math.cosh(t)) * math.cosh(nu * t), 0.0, t_max,
+                    epsabs=0.0, epsrel=1e-13, limit=400)
+        ref = s ** nu * K / (Gamma(nu) * 2.0 ** (nu - 1.0))
+        got = matern.matern_kv(np.array([s]), nu)[0]
+        assert abs(got - ref) <= 1e-10 * abs(ref), (s, got, ref)
+
+
+@pytest.mark.parametrize("nu", GENERAL_NU)
+def test_general_nu_unit_variance_monotone_and_derivative(nu):
+    r = np.linspace(0.0, 3.0, 301)
+    v = matern.matern(r, nu, 0.5)
+    assert v[0] == 1.0 and np.all(np.diff(v) < 0)
+    rho, h = 0.37, 1e-5
+    r = np.linspace(0.01, 2.0, 60)
+    fd = (matern.matern(r, nu, rho * math.exp(h)) - matern.matern(r, nu, rho * math.exp(-h))) / (2 * h)
+    np.testing.assert_allclose(matern.dmatern_dlogrho(r, nu, rho), fd, rtol=1e-7, atol=1e-11)
+
+
+def test_gaussian_is_the_large_nu_limit_of_matern():
+    """Remark after the Matern definition: nu -> inf gives exp(-r^2 / (2 rho^2))."""
+    r = np.linspace(0.0, 2.0, 81)
+    g = matern.matern(r, None, 0.6, family="gaussian")
+    errs = [np.abs(matern.matern(r, nu, 0.6) - g).max() for nu in (10.0, 20.0, 60.0)]
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 4.5e-3
+    h = 1e-5
+    fd = (matern.matern(r, None, 0.6 * math.exp(h), "gaussian") - matern.matern(r, None, 0.6 * math.exp(-h), "gaussian")) / (2 * h)
+    np.testing.assert_allclose(matern.dmatern_dlogrho(r, None, 0.6, "gaussian"), fd, rtol=1e-8, atol=1e-12)
+
+
+def test_anisotropic_distance_follows_the_definition():
+    """r(theta)^2 = (x - y)^T diag(theta) (x - y) (Sec. 3): a hand-worked pair,
+    and Euclidean distances of coordinates scaled by sqrt(theta)."""
+    x, y = np.array([[1.0, 2.0]]), np.array([[4.0, 6.0]])
+    assert matern.distances(x, y, axis=[2.0, 0.5])[0, 0] == math.sqrt(2.0 * 9.0 + 0.5 * 16.0)
+    rng = np.random.default_rng(1)
+    a, b, th = rng.random((6, 3)), rng.random((4, 3)), np.array([0.3, 2.0, 5.0])
+    np.testing.assert_allclose(matern.distances(a, b, th), matern.distances(a * np.sqrt(th), b * np.sqrt(th)),
+                               rtol=1e-14)
 
 
 def test_distances_brute_force():
