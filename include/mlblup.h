@@ -30,9 +30,9 @@
  *    made before its prerequisite returns MLB_ESTATE.
  *    A new mlb_build_basis invalidates the assembly and the solution; a new
  *    mlb_assemble invalidates the solution.
- *  - Matern smoothness nu must be 0.5, 1.5 or 2.5 (closed forms of the
- *    definition in Sec. 3.1); unit variance; the nugget is added on the data
- *    diagonal only.
+ *  - Covariance: Matern of any smoothness 0.2 <= nu <= 30 (Sec. 3.1) or the
+ *    Gaussian kernel (Sec. 8.2), unit variance, Euclidean or anisotropic
+ *    distance (Sec. 3); the nugget is added on the data diagonal only.
  *  - beta is reported on the library's monomial basis: total degree <= w,
  *    graded order, lexicographically decreasing exponents within a degree
  *    (1, x1, .., xd, x1^2, x1 x2, ..), evaluated on coordinates mapped onto
@@ -78,10 +78,18 @@ typedef struct {
     int device;        /* CUDA device ordinal */
 } mlb_opts;
 
+enum { MLB_MATERN = 0, MLB_GAUSSIAN = 1 };
+
 typedef struct {
-    double nu;         /* Matern smoothness: 0.5, 1.5 or 2.5 */
-    double rho;        /* Matern range (> 0) */
+    double nu;         /* Matern smoothness, 0.2 <= nu <= 30 (closed forms at 0.5, 1.5, 2.5;
+                          any other value from the definition with K_nu, Sec. 3.1) */
+    double rho;        /* Matern range, or the width theta of the Gaussian kernel (> 0) */
     double nugget;     /* eta >= 0, added to the covariance of the observations */
+    int family;        /* MLB_MATERN, or MLB_GAUSSIAN: phi(r) = exp(-r^2 / (2 rho^2)) (Sec. 8.2);
+                          nu is ignored for the Gaussian */
+    int naxis;         /* 0: Euclidean distance; d: the anisotropic distance of Sec. 3,
+                          r^2 = sum_k axis[k] (x_k - y_k)^2 */
+    double axis[16];   /* axis weights theta_k > 0 (first naxis entries) */
 } mlb_theta;
 
 typedef struct {
@@ -223,6 +231,14 @@ void mlb_batch_last_phase_ms(double* out);
 int64_t mlb_batch_last_launches(void);
 
 /* ---- inspection (tests and tools) ---------------------------------------- */
+
+/* The covariance function phi(r) of theta (deriv != 0: d phi / d log(rho)) at
+ * n distances r (host arrays; the distance is passed in, so naxis is not
+ * used), evaluated on the host exactly as the kernels evaluate it in FP64: the
+ * closed forms, the Gaussian, or the table of Chebyshev pieces that
+ * mlb_assemble builds for any other smoothness.  Needs no GPU and no context.
+ * MLB_EINVAL for an invalid theta. */
+mlb_status mlb_covariance(const mlb_theta* theta, const double* r, int64_t n, int deriv, double* out);
 
 /* Sizes of the current basis.  Any pointer may be NULL. */
 mlb_status mlb_get_sizes(const mlb_ctx* ctx, int64_t* N, int* d, int* p, int* t, int64_t* nwav);

@@ -44,9 +44,13 @@ def matern_kv(s, nu: float) -> np.ndarray:
     out = np.ones_like(s)
     pos = s > 0
     sp = s[pos]
-    # in logarithms, so that Gamma(nu) 2^(nu-1) and s^nu K_nu(s) stay in range
-    with np.errstate(divide="ignore"):
-        out[pos] = np.exp(nu * np.log(sp) + np.log(_kv(nu, sp)) - _gammaln(nu) - (nu - 1.0) * math.log(2.0))
+    # in logarithms, so that Gamma(nu) 2^(nu-1) and s^nu K_nu(s) stay in range;
+    # where K_nu(s) itself overflows, s is so small that phi = 1 to working
+    # precision (1 - phi ~ s^(2 min(nu, 1)))
+    with np.errstate(divide="ignore", over="ignore", invalid="ignore"):
+        k = _kv(nu, sp)
+        out[pos] = np.where(np.isfinite(k), np.exp(nu * np.log(sp) + np.log(k) - _gammaln(nu)
+                                                   - (nu - 1.0) * math.log(2.0)), 1.0)
     return out
 
 
@@ -57,9 +61,11 @@ def dmatern_kv(s, nu: float) -> np.ndarray:
     out = np.zeros_like(s)
     pos = s > 0
     sp = s[pos]
-    with np.errstate(divide="ignore"):
-        out[pos] = np.exp((nu + 1.0) * np.log(sp) + np.log(_kv(nu - 1.0, sp)) - _gammaln(nu)
-                          - (nu - 1.0) * math.log(2.0))
+    with np.errstate(divide="ignore", over="ignore", invalid="ignore"):
+        k = _kv(nu - 1.0, sp)
+        # where K_{nu-1}(s) overflows, -s phi'(s) ~ s^2 (nu > 1) or s^(2 nu) is below working precision
+        out[pos] = np.where(np.isfinite(k), np.exp((nu + 1.0) * np.log(sp) + np.log(k) - _gammaln(nu)
+                                                   - (nu - 1.0) * math.log(2.0)), 0.0)
     return out
 
 

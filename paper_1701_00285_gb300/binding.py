@@ -34,8 +34,30 @@ class Opts(ctypes.Structure):
                 ("device", ctypes.c_int)]
 
 
+MLB_MATERN, MLB_GAUSSIAN = 0, 1
+FAMILIES = {"matern": MLB_MATERN, "gaussian": MLB_GAUSSIAN}
+
+
 class Theta(ctypes.Structure):
-    _fields_ = [("nu", ctypes.c_double), ("rho", ctypes.c_double), ("nugget", ctypes.c_double)]
+    _fields_ = [("nu", ctypes.c_double), ("rho", ctypes.c_double), ("nugget", ctypes.c_double),
+                ("family", ctypes.c_int), ("naxis", ctypes.c_int), ("axis", ctypes.c_double * 16)]
+
+
+def make_theta(nu: float, rho: float, nugget: float, family: str = "matern", axis=None) -> Theta:
+    """mlb_theta of a Matern (any nu) or Gaussian covariance, with optional
+    axis weights theta_k of the anisotropic distance (None: Euclidean)."""
+    th = Theta()
+    th.nu = float(nu if nu is not None else 0.0)
+    th.rho, th.nugget = float(rho), float(nugget)
+    th.family = FAMILIES[family]
+    if axis is not None:
+        ax = [float(v) for v in axis]
+        if len(ax) > 16:
+            raise ValueError("at most 16 axis weights")
+        th.naxis = len(ax)
+        for i, v in enumerate(ax):
+            th.axis[i] = v
+    return th
 
 
 class Info(ctypes.Structure):
@@ -94,6 +116,7 @@ _SIGS = {
     "mlb_cw_matvec_dev": (ctypes.c_int, [_P, _P, _P]),
     "mlb_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "mlb_get_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    "mlb_covariance": (ctypes.c_int, [ctypes.POINTER(Theta), _P, _I64, ctypes.c_int, _P]),
     "mlb_set_product_variant": (ctypes.c_int, [_P, ctypes.c_int]),
     "mlb_apply_W_noalloc": (ctypes.c_int, [_P, _P, _P]),
     "mlb_get_pattern": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
@@ -152,7 +175,7 @@ def batch_solve(problems, precision: str = "fp64", leaf_size: int = 64, pcg_rtol
         keep += [pts, Z, tg, y, beta]
         a = arr[i]
         a.points, a.n, a.d, a.w = pts.ctypes.data, pts.shape[0], d, q["w"]
-        a.theta = Theta(q["nu"], q["rho"], q["nugget"])
+        a.theta = make_theta(q["nu"], q["rho"], q["nugget"], q.get("family", "matern"), q.get("axis"))
         a.tau_factor = float(q.get("tau_factor", math.inf))
         a.Z, a.targets, a.m = Z.ctypes.data, tg.ctypes.data, tg.shape[0]
         a.yhat, a.beta = y.ctypes.data, beta.ctypes.data
@@ -164,6 +187,18 @@ def batch_solve(problems, precision: str = "fp64", leaf_size: int = 64, pcg_rtol
         import warnings
         warnings.warn("mlb_batch_solve: " + L.mlb_batch_last_error().decode())
     return res, ms.value, st
+
+
+def covariance(r, nu: float, rho: float, family: str = "matern", deriv: bool = False) -> np.ndarray:
+    """phi(r) (or d phi / d log(rho)) as the library's kernels evaluate it in
+    FP64, computed on the host (mlb_covariance; no GPU needed)."""
+    r = _f64(np.atleast_1d(r))
+    out = np.empty_like(r)
+    th = make_theta(nu, rho, 0.0, family)
+    st = lib().mlb_covariance(ctypes.byref(th), _ptr(r), r.size, int(deriv), _ptr(out))
+    if st != 0:
+        raise MLBError(st, "mlb_covariance: invalid covariance parameters")
+    return out
 
 
 def batch_last_launches() -> int:
@@ -232,8 +267,9 @@ class Context:
         self._check(lib().mlb_build_basis_dev(self._h, points_ptr, N, d, w))
         self._sizes()
 
-    def assemble(self, nu: float, rho: float, nugget: float, tau_factor: float = math.inf):
-        th = Theta(nu, rho, nugget)
+    def assemble(self, nu: float, rho: float, nugget: float, tau_factor: float = math.inf,
+                 family: str = "matern", axis=None):
+        th = make_theta(nu, rho, nugget, family, axis)
         self._check(lib().mlb_assemble(self._h, ctypes.byref(th), float(tau_factor)))
 
     def solve(self, Z, check: bool = True):

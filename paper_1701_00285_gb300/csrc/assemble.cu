@@ -134,8 +134,10 @@ struct TileIn {
     const float* xl32;   // mixed: offsets of the points from their leaf's centre, FP32 high part
     const float* xl32lo; //        and low part (offset = high + low to about 1e-14)
     const double* ctr;   // mixed: leaf centres (ncell x d)
-    int d, kind;
-    double scale, nugget;
+    int d;
+    KernelFn K;          // the covariance function
+    double nugget;
+    double sc[kMaxDim];  // per-axis distance scales (FP64 coordinates are scaled as loaded)
     // level pass: children's SS matrix
     const double* SSc;
     int64_t ldSSc;
@@ -206,8 +208,8 @@ __global__ void __launch_bounds__(256) galerkin_tile_kernel(CellTables C, int le
         if (LEAF) {
             const int d = in.d;
             const int64_t bf = C.beg[gf], be = C.beg[ge];
-            for (int idx = tid; idx < sf * d; idx += 256) xf[idx] = in.xs[bf * d + idx];
-            for (int idx = tid; idx < se * d; idx += 256) xe[idx] = in.xs[be * d + idx];
+            for (int idx = tid; idx < sf * d; idx += 256) xf[idx] = in.xs[bf * d + idx] * in.sc[idx % d];
+            for (int idx = tid; idx < se * d; idx += 256) xe[idx] = in.xs[be * d + idx] * in.sc[idx % d];
         }
         __syncthreads();
         if (LEAF) {
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(256) galerkin_tile_kernel(CellTables C, int le
                         const double df = xf[r * d + k] - xe[c * d + k];
                         r2 += df * df;
                     }
-                    v = matern_f64(sqrt(r2), in.kind, in.scale);
+                    v = kern_f64<false>(sqrt(r2), in.K);
                     if (gf == ge && r == c) v += in.nugget;
                 }
                 P[idx] = v;
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(256) galerkin_leaf_f32_kernel(CellTables C, in
     const int ty = tid >> 4, tx = tid & 15;
     const int r0 = ty * 4, c0 = tx * 4;
     const int first = (1 << level) - 1;
-    const ff scale = ff_from_double(in.scale);
+    const ff scale = ff_from_double(in.K.scale);
     for (int64_t pi = blockIdx.x; pi < npairs; pi += gridDim.x) {
         int f, e;
         unrank_pair(pi, f, e);
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(256) galerkin_leaf_f32_kernel(CellTables C, in
                     df = ff_add(df, {dch[k], dcl[k]});
                     r2 = ff_add(r2, ff_mul(df, df));
                 }
-                v = ff_matern(ff_sqrt(r2), in.kind, scale, tab);
+                v = ff_kern<false>(ff_sqrt(r2), in.K, scale, tab);
             }
             P[idx] = v.h;
             Pl[idx] = v.l;
@@ -669,12 +671,12 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
     TileIn in{};
     in.V = ctx->V;
     in.xs = ctx->xs;
-    in.xl32 = ctx->xl32;
-    in.xl32lo = ctx->xl32lo;
-    in.ctr = ctx->leafctr;
+    in.xl32 = ctx->kxl32;
+    in.xl32lo = ctx->kxl32lo;
+    in.ctr = ctx->kctr;
     in.d = ctx->d;
-    in.kind = nu_kind(ctx->theta.nu);
-    in.scale = std::sqrt(2.0 * ctx->theta.nu) / ctx->theta.rho;
+    in.K = ctx->kfn;
+    for (int c = 0; c < kMaxDim; ++c) in.sc[c] = ctx->kgeo.sc[c];
     in.nugget = ctx->theta.nugget;
     for (int l = t; l >= 0; --l) {
         TileOut o;

@@ -476,9 +476,17 @@ mlb_status mlb_assemble(mlb_ctx* ctx, const mlb_theta* th, double tau_factor) {
     if (!ctx || !th) return fail(ctx, MLB_EINVAL, "null argument");
     ctx->err.clear();
     if (ctx->state < 1) return fail(ctx, MLB_ESTATE, "mlb_assemble needs mlb_build_basis first");
-    if (nu_kind(th->nu) < 0) return fail(ctx, MLB_EINVAL, "nu must be 0.5, 1.5 or 2.5");
+    if (th->family != MLB_MATERN && th->family != MLB_GAUSSIAN)
+        return fail(ctx, MLB_EINVAL, "family must be MLB_MATERN or MLB_GAUSSIAN");
+    if (th->family == MLB_MATERN && !(th->nu >= 0.2 && th->nu <= 30.0))
+        return fail(ctx, MLB_EINVAL, "Matern smoothness nu must lie in [0.2, 30]");
     if (!(th->rho > 0) || !std::isfinite(th->rho) || !(th->nugget >= 0) || !std::isfinite(th->nugget))
         return fail(ctx, MLB_EINVAL, "need rho > 0 and nugget >= 0, finite");
+    if (th->naxis != 0 && th->naxis != ctx->d)
+        return fail(ctx, MLB_EINVAL, "naxis must be 0 (Euclidean) or the dimension d");
+    for (int k = 0; k < th->naxis; ++k)
+        if (!(th->axis[k] > 0) || !std::isfinite(th->axis[k]))
+            return fail(ctx, MLB_EINVAL, "axis weights must be positive and finite");
     if (!(tau_factor >= 0)) return fail(ctx, MLB_EINVAL, "tau_factor must be >= 0 or INFINITY");
     cudaSetDevice(ctx->opts.device);
     cudaStreamSynchronize(ctx->stream);
@@ -493,6 +501,10 @@ mlb_status mlb_assemble(mlb_ctx* ctx, const mlb_theta* th, double tau_factor) {
     ctx->theta = *th;
     ctx->tau_factor = tau_factor;
     ctx->state = 1;
+    {
+        mlb_status ks = setup_kernel_fn(ctx);
+        if (ks != MLB_OK) return ks;
+    }
     if (ctx->opts.matrix_free) {
         if (!std::isinf(tau_factor)) return fail(ctx, MLB_EINVAL, "the three-step product needs tau = INFINITY");
         // the kernel sum runs in every PCG iteration: pick its launch shape now,

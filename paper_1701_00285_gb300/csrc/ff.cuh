@@ -6,7 +6,9 @@
 // faster than FP64, so kernel values needed to better than FP32 accuracy are
 // evaluated this way instead of in FP64.
 //
-// ff_exp follows the classical table method: x = k ln2/64 + r with a
+// ff_exp follows Tang's table-driven method ("Table-driven implementation of
+// the exponential function in IEEE floating-point arithmetic", ACM TOMS 15,
+// 1989): x = k ln2/64 + r with a
 // Cody-Waite three-part ln2/64 (the high part has 11 significant bits, so k
 // times it is exact for |k| < 2^13), e^x = 2^(k div 64) * 2^((k mod 64)/64) * e^r,
 // the 64 table values 2^(j/64) as double-float (each CTA fills its shared
@@ -16,6 +18,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include "matern.cuh"
 
 namespace mlb {
 
@@ -137,6 +141,22 @@ __device__ __forceinline__ ff ff_dmatern(ff r, int kind, ff scale, const float2*
 __device__ __forceinline__ ff ff_from_double(double v) {
     const float h = __double2float_rn(v);
     return {h, __double2float_rn(__dsub_rn(v, (double)h))};
+}
+
+// Any covariance function in double-float (DERIV: d phi / d log(rho)):
+// closed-form Matern kinds and the Gaussian on the FP32 pipes; tabulated
+// smoothness through the FP64 table (matern.cuh), split into double-float.
+template <bool DERIV>
+__device__ __forceinline__ ff ff_kern(ff r, const KernelFn& K, ff scale, const float2* tab) {
+    if (K.kind <= KIND_NU_5HALF) return DERIV ? ff_dmatern(r, K.kind, scale, tab) : ff_matern(r, K.kind, scale, tab);
+    if (K.kind == KIND_GAUSS) {
+        const ff s = ff_mul(scale, r);
+        const ff h2 = ff_mul_f(ff_mul(s, s), 0.5f);
+        const ff g = ff_exp({-h2.h, -h2.l}, tab);
+        return DERIV ? ff_mul(ff_mul(s, s), g) : g;
+    }
+    const double s = ((double)r.h + (double)r.l) * K.scale;
+    return ff_from_double(table_f64(K.tab, K.noct, K.nhi, s, DERIV ? 1 : 0));
 }
 
 }  // namespace mlb

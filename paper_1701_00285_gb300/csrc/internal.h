@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/mlblup.h"
+#include "matern.cuh"
 
 namespace mlb {
 
@@ -123,6 +124,14 @@ struct SymPanels {
     int* err = nullptr;         // device flag: bit 0 set when a bounded wait of the product gave up
 };
 
+// Data box centre and per-axis scale sqrt(theta_k) of the kernel distance
+// (1 on every axis for the isotropic distance); the kernels read coordinates
+// as (x - c) sc or x sc.
+struct KGeo {
+    double c[kMaxDim];
+    double sc[kMaxDim];
+};
+
 struct PcgState {
     double rz, rr, bb, alpha, beta, pq;
     int it, done, status;
@@ -174,6 +183,13 @@ struct mlb_ctx {
 
     // assembly
     mlb_theta theta{};
+    mlb::KernelFn kfn{};           // covariance function of the assembly (kernelfn.cu)
+    mlb::KGeo kgeo{};              // data box centre and per-axis distance scales
+    const float* kxs32 = nullptr;  // FP32 coordinates the kernels read: the basis arrays,
+    const float* kxs32lo = nullptr;//   or scaled copies for an anisotropic distance
+    const float* kxl32 = nullptr;
+    const float* kxl32lo = nullptr;
+    const double* kctr = nullptr;
     double tau_factor = 0;
     mlb::Panels pan;
     mlb::SymPanels sym;            // mixed path, complete pattern: each symmetric pair stored once
@@ -228,6 +244,9 @@ mlb_status apply_W_dev(mlb_ctx* ctx, const double* v_kd, double* out);    // N (
 mlb_status apply_Wt_dev(mlb_ctx* ctx, const double* u, double* out_kd);   // nwav -> N (kd)
 mlb_status gather_kd(mlb_ctx* ctx, const double* v_user, double* v_kd);   // caller -> kd order
 mlb_status scatter_kd(mlb_ctx* ctx, const double* v_kd, double* v_user);  // kd -> caller order
+// kernelfn.cu: kind, scale and table of the covariance function, scaled
+// coordinates of an anisotropic distance (allocations in arena_asm)
+mlb_status setup_kernel_fn(mlb_ctx* ctx);
 // assemble.cu
 mlb_status assemble_dev(mlb_ctx* ctx);
 // symv.cu: the symmetric packed FP32 storage (from the FP64 panels of a

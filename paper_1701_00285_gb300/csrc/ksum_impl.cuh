@@ -31,9 +31,6 @@
 
 namespace mlb {
 
-struct Box3 {
-    double c[kMaxDim];
-};
 
 struct TrendArgs {
     const double* beta;   // nullptr: no trend
@@ -62,21 +59,21 @@ __device__ __forceinline__ void add_trend(double& acc, const double* y, const Tr
 template <int D, bool DERIV>
 __global__ void __launch_bounds__(128) ksum_f64_kernel(const double* __restrict__ tg, int64_t M,
                                                        const double* __restrict__ xs,
-                                                       const double* __restrict__ a, int64_t N, int kind,
-                                                       double scale, double* __restrict__ out, TrendArgs tr,
+                                                       const double* __restrict__ a, int64_t N, KernelFn K,
+                                                       KGeo geo, double* __restrict__ out, TrendArgs tr,
                                                        int64_t jchunk, double* __restrict__ part) {
     __shared__ double sx[128 * D];
     __shared__ double sa[128];
     const int64_t k = blockIdx.x * 128LL + threadIdx.x;
     double y[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) y[c] = k < M ? tg[k * D + c] : 0.0;
+    for (int c = 0; c < D; ++c) y[c] = k < M ? tg[k * D + c] * geo.sc[c] : 0.0;
     double acc = 0.0;
     const int64_t jb = blockIdx.y * jchunk, je = min(N, jb + jchunk);
     for (int64_t j0 = jb; j0 < je; j0 += 128) {
         const int nj = (int)(je - j0 < 128 ? je - j0 : 128);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < nj * D; idx += 128) sx[idx] = xs[j0 * D + idx];
+        for (int idx = threadIdx.x; idx < nj * D; idx += 128) sx[idx] = xs[j0 * D + idx] * geo.sc[idx % D];
         if (threadIdx.x < nj) sa[threadIdx.x] = a[j0 + threadIdx.x];
         __syncthreads();
         for (int j = 0; j < nj; ++j) {
@@ -87,7 +84,7 @@ __global__ void __launch_bounds__(128) ksum_f64_kernel(const double* __restrict_
                 r2 += df * df;
             }
             const double r = sqrt(r2);
-            acc += (DERIV ? dmatern_dlogrho_f64(r, kind, scale) : matern_f64(r, kind, scale)) * sa[j];
+            acc += kern_f64<DERIV>(r, K) * sa[j];
         }
     }
     if (k >= M) return;
@@ -95,17 +92,26 @@ __global__ void __launch_bounds__(128) ksum_f64_kernel(const double* __restrict_
         part[blockIdx.y * M + k] = acc;
         return;
     }
-    if (tr.beta) add_trend<D>(acc, y, tr);
+    if (tr.beta) {
+        // the trend is a polynomial in the caller's coordinates, not in the
+        // scaled ones of an anisotropic distance
+        double yy[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) yy[c] = tg[k * D + c];
+        add_trend<D>(acc, yy, tr);
+    }
     out[k] = acc;
 }
 
 // Mixed: FP32 kernel values, FP32 sum per tile of 256 points, FP64 across tiles.
-template <int D, int TPT, bool DERIV, int BS>
+// GEN = false: the half-integer Matern closed forms only (the hot loop of the
+// matrix-free product carries no code for the other covariance kinds).
+template <int D, int TPT, bool DERIV, int BS, bool GEN>
 __global__ void __launch_bounds__(BS) ksum_f32_kernel(const double* __restrict__ tg, int64_t M,
                                                        const float* __restrict__ xs32,
                                                        const double* __restrict__ src64,
-                                                       const double* __restrict__ a, int64_t N, int kind,
-                                                       float scale, Box3 ctr, double* __restrict__ out,
+                                                       const double* __restrict__ a, int64_t N, KernelFn K,
+                                                       KGeo ctr, double* __restrict__ out,
                                                        TrendArgs tr, int64_t jchunk, double* __restrict__ part) {
     constexpr int TS = 256;
     __shared__ float sx[TS * D];
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(BS) ksum_f32_kernel(const double* __restrict__
     for (int t = 0; t < TPT; ++t)
 #pragma unroll
         for (int c = 0; c < D; ++c)
-            y[t][c] = k0 + t < M ? (float)(tg[(k0 + t) * D + c] - ctr.c[c]) : 0.0f;
+            y[t][c] = k0 + t < M ? (float)((tg[(k0 + t) * D + c] - ctr.c[c]) * ctr.sc[c]) : 0.0f;
     double acc[TPT];
 #pragma unroll
     for (int t = 0; t < TPT; ++t) acc[t] = 0.0;
@@ -129,7 +135,7 @@ __global__ void __launch_bounds__(BS) ksum_f32_kernel(const double* __restrict__
             for (int idx = threadIdx.x; idx < nj * D; idx += BS) sx[idx] = xs32[j0 * D + idx];
         } else {
             for (int idx = threadIdx.x; idx < nj * D; idx += BS)
-                sx[idx] = (float)(src64[j0 * D + idx] - ctr.c[idx % D]);
+                sx[idx] = (float)((src64[j0 * D + idx] - ctr.c[idx % D]) * ctr.sc[idx % D]);
         }
         for (int idx = threadIdx.x; idx < nj; idx += BS) {
             const double w = a[j0 + idx];
@@ -155,7 +161,8 @@ __global__ void __launch_bounds__(BS) ksum_f32_kernel(const double* __restrict__
                     r2 = fmaf(df, df, r2);
                 }
                 const float r = sqrtf(r2);
-                const float kv = DERIV ? dmatern_dlogrho_f32(r, kind, scale) : matern_f32(r, kind, scale);
+                const float kv = GEN ? kern_f32<DERIV>(r, K)
+                                     : (DERIV ? dmatern_dlogrho_f32(r, K.kind, K.scale32) : matern_f32(r, K.kind, K.scale32));
                 sum2_add(part[t], comp[t], __fmul_rn(kv, aj));
                 low[t] = fmaf(kv, alj, low[t]);
             }
@@ -192,22 +199,22 @@ __global__ void __launch_bounds__(128) ksum_ff_kernel(const double* __restrict__
                                                       const float* __restrict__ xh32,
                                                       const float* __restrict__ xl32,
                                                       const double* __restrict__ src64,
-                                                      const double* __restrict__ a, int64_t N, int kind,
-                                                      double scale, Box3 ctr, double* __restrict__ out,
+                                                      const double* __restrict__ a, int64_t N, KernelFn K,
+                                                      KGeo ctr, double* __restrict__ out,
                                                       TrendArgs tr, int64_t jchunk, double* __restrict__ part) {
     constexpr int TS = 128;
     __shared__ float sxh[TS * D], sxl[TS * D];
     __shared__ float sah[TS], sal[TS];
     __shared__ float2 tab[64];
     ff_fill_exp2_table(tab);
-    const ff sc = ff_from_double(scale);
+    const ff sc = ff_from_double(K.scale);
     const int64_t k0 = (blockIdx.x * 128LL + threadIdx.x) * TPT;
     ff y[TPT][D];
 #pragma unroll
     for (int t = 0; t < TPT; ++t)
 #pragma unroll
         for (int c = 0; c < D; ++c)
-            y[t][c] = ff_from_double(k0 + t < M ? tg[(k0 + t) * D + c] - ctr.c[c] : 0.0);
+            y[t][c] = ff_from_double(k0 + t < M ? (tg[(k0 + t) * D + c] - ctr.c[c]) * ctr.sc[c] : 0.0);
     double acc[TPT];
 #pragma unroll
     for (int t = 0; t < TPT; ++t) acc[t] = 0.0;
@@ -222,7 +229,7 @@ __global__ void __launch_bounds__(128) ksum_ff_kernel(const double* __restrict__
             }
         } else {
             for (int idx = threadIdx.x; idx < nj * D; idx += 128) {
-                const ff v = ff_from_double(src64[j0 * D + idx] - ctr.c[idx % D]);
+                const ff v = ff_from_double((src64[j0 * D + idx] - ctr.c[idx % D]) * ctr.sc[idx % D]);
                 sxh[idx] = v.h;
                 sxl[idx] = v.l;
             }
@@ -248,7 +255,7 @@ __global__ void __launch_bounds__(128) ksum_ff_kernel(const double* __restrict__
                     r2 = ff_add(r2, ff_mul(df, df));
                 }
                 const ff r = ff_sqrt(r2);
-                const ff kv = DERIV ? ff_dmatern(r, kind, sc, tab) : ff_matern(r, kind, sc, tab);
+                const ff kv = ff_kern<DERIV>(r, K, sc, tab);
                 const float pr = __fmul_rn(kv.h, ah);
                 sum2_add(part[t], comp[t], pr);
                 low[t] = fmaf(kv.h, al, fmaf(kv.l, ah, __fadd_rn(low[t], fmaf(kv.h, ah, -pr))));
@@ -332,14 +339,14 @@ constexpr int kVarBs[kKsumVariants] = {128, 128, 128, 256, 256, 256};
 
 constexpr bool tuned_dim(int D) { return D == 2 || D == 3 || D == 4 || D == 5 || D == 6 || D == 8 || D == 10; }
 
-template <int D, bool DERIV, int TPT, int BS>
+template <int D, bool DERIV, int TPT, int BS, bool GEN = false>
 static void launch_f32_shape(mlb_ctx* ctx, const double* tg, int64_t M, const float* xs32, const double* src,
-                             const double* a, int64_t Ns, int kind, float scale, const Box3& ctr, double* out,
+                             const double* a, int64_t Ns, const KernelFn& K, const KGeo& ctr, double* out,
                              const TrendArgs& tr) {
     const int64_t ctasM = (M + (int64_t)BS * TPT - 1) / ((int64_t)BS * TPT);
     const KsumSplit sp = ksum_split(ctx, ctasM, M, Ns, 256);
     const dim3 grid((unsigned)ctasM, (unsigned)sp.splits);
-    ksum_f32_kernel<D, TPT, DERIV, BS><<<grid, BS, 0, ctx->stream>>>(tg, M, xs32, src, a, Ns, kind, scale, ctr, out,
+    ksum_f32_kernel<D, TPT, DERIV, BS, GEN><<<grid, BS, 0, ctx->stream>>>(tg, M, xs32, src, a, Ns, K, ctr, out,
                                                                      tr, sp.chunk,
                                                                      sp.splits > 1 ? ctx->ksum_part : nullptr);
     launch_reduce<D>(ctx, sp, tg, M, out, tr);
@@ -347,49 +354,49 @@ static void launch_f32_shape(mlb_ctx* ctx, const double* tg, int64_t M, const fl
 
 template <int D, bool DERIV>
 static void launch_f32_variant(int v, mlb_ctx* ctx, const double* tg, int64_t M, const float* xs32,
-                               const double* src, const double* a, int64_t Ns, int kind, float scale,
-                               const Box3& ctr, double* out, const TrendArgs& tr) {
+                               const double* src, const double* a, int64_t Ns, const KernelFn& K,
+                               const KGeo& ctr, double* out, const TrendArgs& tr) {
+    if (K.kind > KIND_NU_5HALF) {
+        launch_f32_shape<D, DERIV, 4, 128, true>(ctx, tg, M, xs32, src, a, Ns, K, ctr, out, tr);
+        return;
+    }
     if constexpr (tuned_dim(D) && !DERIV) {
         switch (v) {
-            case 0: launch_f32_shape<D, DERIV, 2, 128>(ctx, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
-            case 2: launch_f32_shape<D, DERIV, 8, 128>(ctx, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
-            case 3: launch_f32_shape<D, DERIV, 2, 256>(ctx, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
-            case 4: launch_f32_shape<D, DERIV, 4, 256>(ctx, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
-            case 5: launch_f32_shape<D, DERIV, 8, 256>(ctx, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr); return;
+            case 0: launch_f32_shape<D, DERIV, 2, 128>(ctx, tg, M, xs32, src, a, Ns, K, ctr, out, tr); return;
+            case 2: launch_f32_shape<D, DERIV, 8, 128>(ctx, tg, M, xs32, src, a, Ns, K, ctr, out, tr); return;
+            case 3: launch_f32_shape<D, DERIV, 2, 256>(ctx, tg, M, xs32, src, a, Ns, K, ctr, out, tr); return;
+            case 4: launch_f32_shape<D, DERIV, 4, 256>(ctx, tg, M, xs32, src, a, Ns, K, ctr, out, tr); return;
+            case 5: launch_f32_shape<D, DERIV, 8, 256>(ctx, tg, M, xs32, src, a, Ns, K, ctr, out, tr); return;
             default: break;
         }
     }
-    launch_f32_shape<D, DERIV, 4, 128>(ctx, tg, M, xs32, src, a, Ns, kind, scale, ctr, out, tr);
+    launch_f32_shape<D, DERIV, 4, 128>(ctx, tg, M, xs32, src, a, Ns, K, ctr, out, tr);
 }
 
 template <int D, bool DERIV>
 static void launch_ksum(mlb_ctx* ctx, const double* tg, int64_t M, const double* src, int64_t Ns,
                         const double* a, double* out, TrendArgs tr, bool accurate) {
-    const int kind = nu_kind(ctx->theta.nu);
-    const double scale = std::sqrt(2.0 * ctx->theta.nu) / ctx->theta.rho;
+    const KernelFn& K = ctx->kfn;
+    const KGeo& geo = ctx->kgeo;
     if (ctx->opts.precision == MLB_MIXED && accurate) {
-        Box3 ctr;
-        for (int c = 0; c < kMaxDim; ++c) ctr.c[c] = c < ctx->d ? 0.5 * (ctx->box_lo[c] + ctx->box_hi[c]) : 0.0;
         constexpr int TPT = 2;
         const int64_t ctasM = (M + 128 * TPT - 1) / (128 * TPT);
         const KsumSplit sp = ksum_split(ctx, ctasM, M, Ns, 128);
         ksum_ff_kernel<D, TPT, DERIV><<<dim3((unsigned)ctasM, (unsigned)sp.splits), 128, 0, ctx->stream>>>(
-            tg, M, src ? nullptr : ctx->xs32, src ? nullptr : ctx->xs32lo, src, a, Ns, kind, scale, ctr, out, tr,
+            tg, M, src ? nullptr : ctx->kxs32, src ? nullptr : ctx->kxs32lo, src, a, Ns, K, geo, out, tr,
             sp.chunk, sp.splits > 1 ? ctx->ksum_part : nullptr);
         launch_reduce<D>(ctx, sp, tg, M, out, tr);
         return;
     }
     if (ctx->opts.precision == MLB_MIXED) {
-        Box3 ctr;
-        for (int c = 0; c < kMaxDim; ++c) ctr.c[c] = c < ctx->d ? 0.5 * (ctx->box_lo[c] + ctx->box_hi[c]) : 0.0;
-        launch_f32_variant<D, DERIV>(DERIV ? 1 : ctx->ksum_variant, ctx, tg, M, src ? nullptr : ctx->xs32, src,
-                                     a, Ns, kind, (float)scale, ctr, out, tr);
+        launch_f32_variant<D, DERIV>(DERIV ? 1 : ctx->ksum_variant, ctx, tg, M, src ? nullptr : ctx->kxs32, src,
+                                     a, Ns, K, geo, out, tr);
         return;
     }
     const int64_t ctasM = (M + 127) / 128;
     const KsumSplit sp = ksum_split(ctx, ctasM, M, Ns, 128);
     ksum_f64_kernel<D, DERIV><<<dim3((unsigned)ctasM, (unsigned)sp.splits), 128, 0, ctx->stream>>>(
-        tg, M, src ? src : ctx->xs, a, Ns, kind, scale, out, tr, sp.chunk, sp.splits > 1 ? ctx->ksum_part : nullptr);
+        tg, M, src ? src : ctx->xs, a, Ns, K, geo, out, tr, sp.chunk, sp.splits > 1 ? ctx->ksum_part : nullptr);
     launch_reduce<D>(ctx, sp, tg, M, out, tr);
 }
 

@@ -177,7 +177,13 @@ def test_call_order_and_argument_errors(pkg):
         ctx.solve(P.Z)
     assert e.value.name == "ESTATE"
     with pytest.raises(pkg.MLBError) as e:
-        ctx.assemble(0.75, 0.3, 0.0)
+        ctx.assemble(0.1, 0.3, 0.0)          # smoothness below the supported range
+    assert e.value.name == "EINVAL"
+    with pytest.raises(pkg.MLBError) as e:
+        ctx.assemble(1.5, 0.3, 0.0, axis=[1.0, -2.0])
+    assert e.value.name == "EINVAL"
+    with pytest.raises(pkg.MLBError) as e:
+        ctx.assemble(1.5, 0.3, 0.0, axis=[1.0, 2.0, 3.0])   # d = 2
     assert e.value.name == "EINVAL"
     with pytest.raises(pkg.MLBError) as e:
         ctx.assemble(1.5, -1.0, 0.0)
