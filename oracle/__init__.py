@@ -23,6 +23,8 @@ What it computes, in the paper's order and notation:
                   residual (Sec. 6.2).
 * ``dense``    -- the classic GLS/BLUP formulae (eqs. GLSbeta, KrigBLUP) and the
                   saddle-point system (eq. Spatial:problem).
+* ``dense_mp`` -- the saddle-point system solved at 100 digits (mpmath) for
+                  the ill-conditioned accuracy study of Sec. 8.2 (Table 5).
 * ``mlblup``   -- the multilevel predictor (eqs. Spatial:eqn1-3, Spatial).
 * ``grad``     -- gradient of a held-out prediction loss in log(rho) and
                   log(nugget) by the adjoint of the saddle-point system (the

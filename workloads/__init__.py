@@ -32,7 +32,7 @@ BASE_SEED = 170100285
 
 __all__ = [
     "BASE_SEED", "Problem", "dense_2d", "clustered_3d", "uniform_10d", "batched_problems",
-    "heldout_5d", "small_problem", "subsample",
+    "heldout_5d", "small_problem", "subsample", "unit_disk_gaussian", "TABLE5_ROWS",
 ]
 
 
@@ -43,8 +43,8 @@ class Problem:
     points: np.ndarray          # (N, d) float64, user order
     Z: np.ndarray               # (N,) float64 observations
     targets: np.ndarray         # (M, d) float64 prediction locations
-    nu: float                   # Matern smoothness (1/2, 3/2 or 5/2)
-    rho: float                  # Matern range
+    nu: float                   # Matern smoothness
+    rho: float                  # Matern range (Gaussian kernel: its width theta)
     nugget: float               # variance added on the data diagonal
     w: int                      # total degree of the polynomial trend space
     leaf_size: int              # kd-tree leaf size n0
@@ -52,6 +52,7 @@ class Problem:
     pcg_rtol: float = 1e-10
     y_targets: np.ndarray | None = None   # held-out observations (differentiation config)
     meta: dict = field(default_factory=dict)
+    family: str = "matern"      # or "gaussian"
 
     @property
     def N(self) -> int:
@@ -198,6 +199,32 @@ def heldout_5d(N: int = 32768, M: int = 4096) -> Problem:
                    y_targets=yt, meta={"trend_coef": coef, "omega": omega})
 
 
+# (alpha, theta) of the rows of the paper's accuracy table (Sec. 8.2, Table 5)
+TABLE5_ROWS = ((1.0, 10.0), (0.5, 10.0), (2.0, 10.0), (2.0, 3.0), (0.5, 3.0))
+
+
+def unit_disk_gaussian(alpha: float, theta: float, N: int = 200, M: int = 200) -> Problem:
+    """The ill-conditioned accuracy study (Sec. 8.2, Table 5): N points drawn
+    uniformly on the unit disk (radius sqrt(U), angle 2 pi V), the Gaussian
+    kernel exp(-r^2 / (2 theta^2)), no nugget, trend degree w = 8 (p = 45),
+    observations Z = 1 + sin(alpha x1) sin(alpha x2) without noise, M targets
+    drawn the same way.  The paper does not give its points; these are one
+    seeded draw, the same for every (alpha, theta)."""
+    r_pts, r_tgt = _streams(6, 2)
+
+    def disk(rng, n):
+        rad = np.sqrt(rng.uniform(0.0, 1.0, size=n))
+        ang = 2.0 * np.pi * rng.uniform(0.0, 1.0, size=n)
+        return np.stack([rad * np.cos(ang), rad * np.sin(ang)], axis=1)
+
+    x = disk(r_pts, N)
+    tg = disk(r_tgt, M)
+    z = 1.0 + np.sin(alpha * x[:, 0]) * np.sin(alpha * x[:, 1])
+    return Problem(f"unit_disk_gaussian_a{alpha:g}_t{theta:g}", x, z, tg, nu=math.inf, rho=theta,
+                   nugget=0.0, w=8, leaf_size=64, tau_factor=math.inf, pcg_rtol=1e-14,
+                   meta={"alpha": alpha, "theta": theta}, family="gaussian")
+
+
 def small_problem(seed: int, N: int, d: int, w: int, nu: float = 1.5, rho: float = 0.3,
                   nugget: float = 1e-6, leaf_size: int = 16, tau_factor: float = math.inf,
                   M: int = 32, clustered: bool = False, with_y: bool = False) -> Problem:
@@ -234,4 +261,4 @@ def subsample(prob: Problem, n: int, seed: int = 0, m: int | None = None) -> Pro
     return Problem(prob.name + f"_sub{n}", prob.points[idx].copy(), prob.Z[idx].copy(),
                    tg.copy(), prob.nu, prob.rho, prob.nugget, prob.w, prob.leaf_size,
                    prob.tau_factor, prob.pcg_rtol, None if yt is None else yt.copy(),
-                   dict(prob.meta))
+                   dict(prob.meta), prob.family)
