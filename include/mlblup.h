@@ -260,8 +260,9 @@ mlb_status mlb_cw_matvec(mlb_ctx* ctx, const double* u, double* out);
 mlb_status mlb_cw_matvec_dev(mlb_ctx* ctx, const double* u_dev, double* out_dev);
 
 /* W v like mlb_apply_W, for callers that cannot allocate device memory at the
- * moment they need it (inside CUDA graph capture, in loops that must not block
- * on the allocator, under a memory pool they do not own).  The paper has no
+ * moment they need it (loops that must not block on the allocator, processes
+ * held to a fixed device-memory budget, hosts whose device memory belongs to
+ * another framework's pool).  The paper has no
  * counterpart: it only changes where the work space lives.  v_dev (N doubles,
  * caller order) and out_dev (N - p doubles) are device buffers owned by the
  * caller; the work space is one fixed 4 MiB array in device memory that every

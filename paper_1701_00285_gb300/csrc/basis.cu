@@ -326,10 +326,10 @@ mlb_status scatter_kd(mlb_ctx* ctx, const double* v_kd, double* v_user) {
 // ---------------------------------------------------------------------------
 // W v without any device allocation.
 //
-// Some callers cannot allocate device memory when they need W v: code that
-// runs while a CUDA graph is being captured (cudaMalloc is not allowed inside
-// a capture), real-time loops that must not block on the allocator, and hosts
-// whose device memory is managed by a pool they do not own.  For them this
+// Some callers cannot allocate device memory when they need W v: real-time
+// loops that must not block on the allocator (cudaMalloc can synchronise the
+// device), processes held to a fixed device-memory budget, and hosts whose
+// device memory is owned by another framework's pool.  For them this
 // entry point keeps its work space -- the input reordered into kd-tree order
 // and the scaling coefficients of every level -- in one fixed array in device
 // global memory that every GPU loading this library reserves until the

@@ -60,6 +60,20 @@ static __device__ void pcg_alpha_finish(const double* part, int nparts, PcgState
     st->alpha = st->rz / pq;
 }
 
+// Part of q_i (right-hand side rhs) of the symmetric packed product: the
+// slots k = first, first + step, ... of the list (row sums of the segments of
+// row i's block, then column sums of the blocks above it), added in order.
+static __device__ __forceinline__ double sym_q_slots(const SymPanels& S, int64_t n, int64_t i, int rhs, int first,
+                                                     int step) {
+    const int b = (int)(i / kSymRows);
+    const int ns = sym_nseg(n, b, S.seg);
+    const float* rp = S.rowpart + (int64_t)rhs * S.nsegCap * n + i;
+    const float* cp = S.colpart + (int64_t)rhs * S.nblk * n + i;
+    double q = 0.0;
+    for (int k = first; k < ns + b; k += step) q += (double)(k < ns ? rp[(int64_t)k * n] : cp[(int64_t)(k - ns) * n]);
+    return q;
+}
+
 // q_i (right-hand side rhs) of the symmetric packed product: the row sums of
 // the segments of row i's block, then the column sums of the blocks above it,
 // always in this order, so the result does not depend on scheduling.

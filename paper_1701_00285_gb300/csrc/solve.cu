@@ -335,47 +335,10 @@ __global__ void __launch_bounds__(256) pcg_alpha_kernel(const double* part, int 
     st->alpha = st->rz / pq;
 }
 
-// x += alpha p, r -= alpha q, z = P^{-1} r and the partials of r.r and r.z;
-// the last CTA then forms beta and the stopping test, and (fuse_p) also
+// The last CTA of a vector update: beta, the stopping test and (fuse_p)
 // p = z + beta p, which is cheaper than another launch for short vectors.
-// With ypart != nullptr, q_i is the in-order sum of the FP32 product's
-// segment partials (nseg[rowCell[i]] of them); with the symmetric packed
-// storage, the in-order sum of its row and column partials (sym_q).
-__global__ void pcg_update_xr_kernel(int64_t n, PcgState* st, double* __restrict__ p,
-                                     const double* __restrict__ q, const double* __restrict__ ypart,
-                                     const int* __restrict__ rowCell, const int* __restrict__ nseg,
-                                     SymPanels sym, const double* __restrict__ diag,
-                                     double* x, double* r, double* z, double* part, double tol2, int maxit,
-                                     int fuse_p, float* xh, float* xl) {
-    if (st->done) return;
-    const double alpha = st->alpha;
-    double rr = 0.0, rz = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double qi;
-        if (sym.vals) {
-            qi = sym_q(sym, n, i, 0);
-        } else if (ypart) {
-            const int ns = nseg[rowCell[i]];
-            qi = 0.0;
-            for (int sg = 0; sg < ns; ++sg) qi += ypart[sg * n + i];
-        } else {
-            qi = q[i];
-        }
-        x[i] += alpha * p[i];
-        const double ri = r[i] - alpha * qi;
-        r[i] = ri;
-        const double zi = diag ? ri / diag[i] : ri;
-        z[i] = zi;
-        rr += ri * ri;
-        rz += ri * zi;
-    }
-    const double s1 = block_reduce(rr);
-    const double s2 = block_reduce(rz);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = s1;
-        part[kVecBlocks + blockIdx.x] = s2;
-    }
-    if (!draw_last_ticket(st)) return;
+__device__ void pcg_update_finish(int64_t n, PcgState* st, const double* part, double tol2, int maxit, int fuse_p,
+                                  double* __restrict__ p, const double* z, float* xh, float* xl) {
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
         a += __ldcg(part + i);
@@ -408,6 +371,90 @@ __global__ void pcg_update_xr_kernel(int64_t n, PcgState* st, double* __restrict
             p[i] = v;
             store_split(xh, xl, i, v);
         }
+}
+
+// x += alpha p, r -= alpha q, z = P^{-1} r and the partials of r.r and r.z;
+// the last CTA then finishes the iteration (pcg_update_finish).
+// With ypart != nullptr, q_i is the in-order sum of the FP32 product's
+// segment partials (nseg[rowCell[i]] of them); otherwise q is read.
+__global__ void pcg_update_xr_kernel(int64_t n, PcgState* st, double* __restrict__ p,
+                                     const double* __restrict__ q, const double* __restrict__ ypart,
+                                     const int* __restrict__ rowCell, const int* __restrict__ nseg,
+                                     const double* __restrict__ diag,
+                                     double* x, double* r, double* z, double* part, double tol2, int maxit,
+                                     int fuse_p, float* xh, float* xl) {
+    if (st->done) return;
+    const double alpha = st->alpha;
+    double rr = 0.0, rz = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double qi;
+        if (ypart) {
+            const int ns = nseg[rowCell[i]];
+            qi = 0.0;
+            for (int sg = 0; sg < ns; ++sg) qi += ypart[sg * n + i];
+        } else {
+            qi = q[i];
+        }
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * qi;
+        r[i] = ri;
+        const double zi = diag ? ri / diag[i] : ri;
+        z[i] = zi;
+        rr += ri * ri;
+        rz += ri * zi;
+    }
+    const double s1 = block_reduce(rr);
+    const double s2 = block_reduce(rz);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = s1;
+        part[kVecBlocks + blockIdx.x] = s2;
+    }
+    if (!draw_last_ticket(st)) return;
+    pcg_update_finish(n, st, part, tol2, maxit, fuse_p, p, z, xh, xl);
+}
+
+// The same update after the symmetric packed product: q_i is the sum of up to
+// (segments + blocks above) partials, too many for one thread to read in
+// sequence.  A CTA takes 32 consecutive elements at a time (one row block, so
+// the slot count is uniform); its eight warps each add every eighth slot
+// (reads coalesced along the elements), and warp 0 adds the eight sums in
+// order and updates the vectors.  The order is fixed, so q is deterministic.
+__global__ void __launch_bounds__(256) pcg_update_sym_kernel(int64_t n, PcgState* st, double* __restrict__ p,
+                                                          SymPanels S, const double* __restrict__ diag,
+                                                          double* x, double* r, double* z, double* part,
+                                                          double tol2, int maxit, int fuse_p, float* xh,
+                                                          float* xl) {
+    if (st->done) return;
+    __shared__ double qs[8][32];
+    const double alpha = st->alpha;
+    const int j = threadIdx.x & 31, g = threadIdx.x >> 5;
+    double rr = 0.0, rz = 0.0;
+    for (int64_t c0 = (int64_t)blockIdx.x * 32; c0 < n; c0 += (int64_t)gridDim.x * 32) {
+        const int64_t i = c0 + j;
+        qs[g][j] = i < n ? sym_q_slots(S, n, i, 0, g, 8) : 0.0;
+        __syncthreads();
+        if (g == 0 && i < n) {
+            double qi = qs[0][j];
+#pragma unroll
+            for (int k = 1; k < 8; ++k) qi += qs[k][j];
+            x[i] += alpha * p[i];
+            const double ri = r[i] - alpha * qi;
+            r[i] = ri;
+            const double zi = diag ? ri / diag[i] : ri;
+            z[i] = zi;
+            rr += ri * ri;
+            rz += ri * zi;
+        }
+        __syncthreads();
+    }
+    const double s1 = block_reduce(rr);
+    const double s2 = block_reduce(rz);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = s1;
+        part[kVecBlocks + blockIdx.x] = s2;
+    }
+    if (!draw_last_ticket(st)) return;
+    pcg_update_finish(n, st, part, tol2, maxit, fuse_p, p, z, xh, xl);
 }
 
 __global__ void pcg_update_p_kernel(int64_t n, PcgState* st, const double* __restrict__ z, double* p, float* xh,
@@ -551,11 +598,13 @@ static mlb_status launch_iteration(mlb_ctx* ctx, double* x, double* r, double* z
     const bool segs = !ctx->opts.matrix_free && !ctx->sym.vals && ctx->pan.vals32;
     // short vectors: the last CTA of the update also forms p; long ones get a launch
     const int fuse_p = n <= kFusePMax ? 1 : 0;
-    pcg_update_xr_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, p, q, segs ? ctx->pan.ypart : nullptr,
-                                                     ctx->pan.rowCell, ctx->pan.nseg,
-                                                     ctx->opts.matrix_free ? SymPanels{} : ctx->sym, diag, x, r, z,
-                                                     part2, tol2,
-                                                     ctx->opts.pcg_maxit, fuse_p, split_h(ctx), split_l(ctx));
+    if (!ctx->opts.matrix_free && ctx->sym.vals)
+        pcg_update_sym_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, p, ctx->sym, diag, x, r, z, part2, tol2,
+                                                          ctx->opts.pcg_maxit, fuse_p, split_h(ctx), split_l(ctx));
+    else
+        pcg_update_xr_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, p, q, segs ? ctx->pan.ypart : nullptr,
+                                                         ctx->pan.rowCell, ctx->pan.nseg, diag, x, r, z, part2, tol2,
+                                                         ctx->opts.pcg_maxit, fuse_p, split_h(ctx), split_l(ctx));
     ctx->launches += 1;
     if (!fuse_p) {
         pcg_update_p_kernel<<<kVecBlocks, 256, 0, st>>>(n, ctx->pcg, z, p, split_h(ctx), split_l(ctx));

@@ -427,9 +427,23 @@ __global__ void __launch_bounds__(288, 2) sym_spmv_bulk_kernel(SymPanels S, int6
     }
 }
 
-__global__ void sym_reduce_kernel(SymPanels S, int64_t n, double* __restrict__ y) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = sym_q(S, n, i, 0);
+// y = q of right-hand side 0, in the order of the PCG update
+// (pcg_update_sym_kernel): eight warps per 32 elements, every eighth slot each
+__global__ void __launch_bounds__(256) sym_reduce_kernel(SymPanels S, int64_t n, double* __restrict__ y) {
+    __shared__ double qs[8][32];
+    const int j = threadIdx.x & 31, g = threadIdx.x >> 5;
+    for (int64_t c0 = (int64_t)blockIdx.x * 32; c0 < n; c0 += (int64_t)gridDim.x * 32) {
+        const int64_t i = c0 + j;
+        qs[g][j] = i < n ? sym_q_slots(S, n, i, 0, g, 8) : 0.0;
+        __syncthreads();
+        if (g == 0 && i < n) {
+            double q = qs[0][j];
+#pragma unroll
+            for (int k = 1; k < 8; ++k) q += qs[k][j];
+            y[i] = q;
+        }
+        __syncthreads();
+    }
 }
 
 static mlb_status tune_sym(mlb_ctx* ctx);

@@ -1,8 +1,9 @@
 """mlb_apply_W_noalloc: W v computed with a fixed device work space instead of
-allocations, for callers that cannot allocate at that moment (graph capture,
-allocation-free loops).  Collected last on purpose: a failure here leaves every
-other test already run.  Checked against mlb_apply_W on two calls in a row,
-which share the work space."""
+allocations, for callers that cannot allocate at that moment (loops that must
+not block on the allocator, a fixed device-memory budget, memory owned by
+another framework's pool).  Collected last on purpose: a failure here leaves
+every other test already run.  Checked against mlb_apply_W on two calls in a
+row, which share the work space, and at the exact size limit."""
 import math
 
 import numpy as np
@@ -48,3 +49,31 @@ def test_noalloc_transform_rejects_sizes_beyond_its_work_space():
     with pytest.raises(pkg.MLBError) as e:
         ctx.apply_W_noalloc(v.data_ptr(), out.data_ptr())
     assert e.value.name == "EINVAL" and "work space" in str(e.value)
+
+
+def test_noalloc_transform_at_the_exact_size_limit():
+    """d = 2, w = 1 (p = 3), leaf 64: every one of the 2^14 - 1 cells of a
+    depth-13 tree keeps 3 scaling coefficients, so N = 524,288 - 3 (2^14 - 1)
+    fills the work space exactly and one more point exceeds it."""
+    import torch
+    import paper_1701_00285_gb300 as pkg
+
+    n_fit = 524288 - 3 * (2 ** 14 - 1)
+    x = np.random.default_rng(13).random((n_fit + 1, 2))
+    for n, ok in ((n_fit, True), (n_fit + 1, False)):
+        ctx = pkg.Context("fp64", leaf_size=64)
+        ctx.build_basis(x[:n], 1)
+        assert ctx.t == 13
+        v = np.random.default_rng(14).standard_normal(n)
+        v_dev = torch.from_numpy(v).cuda()
+        out = torch.full((ctx.nwav,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        if ok:
+            ctx.apply_W_noalloc(v_dev.data_ptr(), out.data_ptr())
+            torch.cuda.synchronize()
+            np.testing.assert_allclose(out.cpu().numpy(), ctx.apply_W(v), rtol=1e-12, atol=1e-12)
+        else:
+            with pytest.raises(pkg.MLBError) as e:
+                ctx.apply_W_noalloc(v_dev.data_ptr(), out.data_ptr())
+            assert e.value.name == "EINVAL"
+        ctx.close()
