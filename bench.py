@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--targets", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra keys: full-size clustered_3d assembly and uniform_10d product")
     ap.add_argument("--mse", type=int, default=0,
                     help="time the kriging MSE at this many targets instead (one PCG solve each)")
     return ap.parse_args()
@@ -380,6 +382,62 @@ def measure(pkg, torch, P, precision, args, dev, local_rank, world, stream):
     return out
 
 
+def extra_assembly(pkg, torch, stream, local_rank):
+    """The sparse workload's assembly at full size (n = 65,536 in [0,1]^3,
+    half in 8 tight clusters, tau = 2 level-mean diameters): C~_W entries/s
+    in both precisions, timed with CUDA events on the context's stream (the
+    assembly's own device time, mlb_info.ms_assemble).  Its truncated system
+    is indefinite, so no solve is timed."""
+    import workloads as wl
+    P = wl.clustered_3d(M=16)
+    out = {"workload": describe(P)}
+    for prec in ("mixed", "fp64"):
+        ctx = pkg.Context(prec, leaf_size=P.leaf_size, device=local_rank)
+        ctx.set_stream(stream.cuda_stream)
+        ctx.build_basis(P.points, P.w)
+        ms = []
+        for _ in range(3):
+            ctx.assemble(P.nu, P.rho, P.nugget, P.tau_factor)
+            ms.append(ctx.info()["ms_assemble"])
+        inf = ctx.info()
+        ctx.close()
+        t = statistics.median(ms[1:])
+        out[prec] = {"ms_assemble": t, "cw_entries_per_s": inf["nnz_unique"] / (t / 1000.0),
+                     "nnz_unique": inf["nnz_unique"], "nnz_stored": inf["nnz"]}
+    return out
+
+
+def extra_matrix_free_product(pkg, torch, stream, local_rank):
+    """One full-size product of the high-dimensional workload (n = 262,144 in
+    [0,1]^10, nu = 5/2, leaf 128, w = 2): the three-step product W (C (W^T u))
+    whose N x N FP32 kernel sum dominates; CUDA events on the stream."""
+    import workloads as wl
+    P = wl.uniform_10d(M=16)
+    ctx = pkg.Context("mixed", leaf_size=P.leaf_size, matrix_free=True, precond=False, device=local_rank)
+    ctx.set_stream(stream.cuda_stream)
+    ctx.build_basis(P.points, P.w)
+    ctx.assemble(P.nu, P.rho, P.nugget, P.tau_factor)
+    with torch.cuda.stream(stream):
+        u = torch.randn(ctx.nwav, dtype=torch.float64, device=f"cuda:{local_rank}")
+        o = torch.empty_like(u)
+    ctx.cw_matvec_dev(u.data_ptr(), o.data_ptr())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.cw_matvec_dev(u.data_ptr(), o.data_ptr())
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ctx.close()
+    flops = float(P.N) * P.N * ksum_flops_per_pair(P.d)
+    achieved = flops / (ms / 1000.0) / 1e12
+    return {"workload": describe(P), "ms_per_product": ms, "pairs_per_s": float(P.N) * P.N / (ms / 1000.0),
+            "roofline": {"kernel": "ksum_f32_kernel", "bound": "alu", "achieved": achieved,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                         "peak_source": "nominal", "algorithmic_flops": flops}}
+
+
 def e2e_run(ctx, P, args, world, torch, dev=None):
     hp, hz, ht = P.points.copy(), P.Z.copy(), P.targets.copy()
     ctx.set_stream(None)
@@ -582,6 +640,9 @@ def run_ours(args, rank, world, local_rank):
             "rel_beta_err": float(np.linalg.norm(got["beta"] - ref["beta"]) / np.linalg.norm(ref["beta"])),
             "speedup": (head["value"] / other["value"]) if args.precision == "mixed" else (other["value"] / head["value"])}
         other["ctx"].close()
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "heldout_5d" and args.n is None:
+        line["clustered_3d_assembly"] = extra_assembly(pkg, torch, stream, local_rank)
+        line["uniform_10d_product"] = extra_matrix_free_product(pkg, torch, stream, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(P)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "exponent")}
