@@ -108,8 +108,9 @@ typedef struct {
                                   mixed path, FP64 otherwise; 0 when matrix-free) */
     int symmetric;             /* 1: the product streams each symmetric pair of entries once
                                   (mixed path, every cell pair admissible); 0: both triangles */
-    int product_variant;       /* form of the symmetric product: 0 plain loads, 1 bulk-copy
-                                  pipeline (chosen by timing both at assembly) */
+    int product_variant;       /* form of the product chosen by timing at assembly: symmetric
+                                  storage 0 plain loads, 1 bulk-copy pipeline; matrix-free
+                                  kernel sum 0..5 launch shapes, 6 tensor cores */
 } mlb_info;
 
 /* Fills *opts with defaults: FP64, n0 = 64, rtol 1e-10, maxit 20000, diagonal
@@ -281,12 +282,15 @@ mlb_status mlb_apply_W_noalloc(mlb_ctx* ctx, const double* v_dev, double* out_de
  * info: host.  MLB_ESTATE before mlb_assemble. */
 mlb_status mlb_get_info(const mlb_ctx* ctx, mlb_info* info);
 
-/* Forces the form of the symmetric FP32 product (0: plain loads with L2
- * prefetch, 1: bulk-copy pipeline through shared memory), which mlb_assemble
- * otherwise picks by timing both; for tests and measurements.  MLB_ESTATE
- * unless the current assembly uses the symmetric storage; MLB_EINVAL for other
- * values.  The two forms add the FP32 products of a row in different orders,
- * so their results agree to FP32 rounding, not bit for bit. */
+/* Forces the form of the product that mlb_assemble otherwise picks by timing
+ * the candidates; for tests and measurements.  Symmetric FP32 storage: 0 plain
+ * loads with L2 prefetch, 1 bulk-copy pipeline through shared memory (the two
+ * add the FP32 products of a row in different orders, so they agree to FP32
+ * rounding, not bit for bit).  Mixed matrix-free product: the FP32 kernel
+ * sum's launch shape 0..5, or 6 for its tensor-core form (squared distances
+ * as one BF16x3 contraction on the tensor cores; d = 5, 8 or 10 and a
+ * closed-form Matern kind).  MLB_ESTATE for other assemblies; MLB_EINVAL for
+ * values outside these. */
 mlb_status mlb_set_product_variant(mlb_ctx* ctx, int variant);
 
 /* Number of kernels the context has launched since mlb_create. */

@@ -15,7 +15,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",
          "--expt-relaxed-constexpr"]
-SOURCES = ["capi.cu", "kernelfn.cu", "basis.cu", "assemble.cu", "solve.cu", "symv.cu", "ksum.cu", "ksum_hi.cu", "grad.cu", "batch.cu",
+SOURCES = ["capi.cu", "kernelfn.cu", "basis.cu", "assemble.cu", "solve.cu", "symv.cu", "ksum.cu", "ksum_hi.cu", "ksum_tc.cu", "grad.cu", "batch.cu",
            "loglik.cu"]
 
 

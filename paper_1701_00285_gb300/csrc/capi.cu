@@ -687,13 +687,21 @@ mlb_status mlb_get_info(const mlb_ctx* ctx, mlb_info* info) {
     I.product_values = ctx->opts.matrix_free ? 0 : (ctx->sym.vals ? ctx->sym.stored : ctx->pan.stored);
     I.ms_assemble = ctx->ms_assemble;
     I.launches = ctx->launches;
-    I.product_variant = ctx->sym.vals ? ctx->sym_variant : 0;
+    I.product_variant = ctx->sym.vals ? ctx->sym_variant : (ctx->opts.matrix_free ? ctx->ksum_variant : 0);
     *info = I;
     return MLB_OK;
 }
 
 mlb_status mlb_set_product_variant(mlb_ctx* ctx, int variant) {
     if (!ctx) return MLB_EINVAL;
+    if (ctx->state >= 2 && ctx->opts.matrix_free && ctx->opts.precision == MLB_MIXED) {
+        // the matrix-free product: the kernel sum's launch shape, or its tensor-core form
+        if (variant < 0 || variant > kKsumFormTC) return fail(ctx, MLB_EINVAL, "variant must be 0..6");
+        if (variant == kKsumFormTC && !ksum_tc_supported(ctx))
+            return fail(ctx, MLB_EINVAL, "no tensor-core kernel sum for this dimension and covariance");
+        ctx->ksum_variant = variant;
+        return MLB_OK;
+    }
     if (ctx->state < 2 || !ctx->sym.vals) return fail(ctx, MLB_ESTATE, "no symmetric storage in this assembly");
     if (variant != 0 && variant != 1) return fail(ctx, MLB_EINVAL, "variant must be 0 or 1");
     ctx->sym_variant = variant;

@@ -278,6 +278,12 @@ mlb_status kernel_sum_general(mlb_ctx* ctx, const double* targets, int64_t M, co
                               bool accurate = true);
 // picks the FP32 kernel-sum launch shape for this context (ksum.cu)
 mlb_status tune_kernel_sum(mlb_ctx* ctx);
+// ksum_tc.cu: the matrix-free product's kernel sum (targets = sources = the
+// data points) on the tensor cores; false when the dimension or covariance
+// kind has no tensor-core form (then nothing is launched)
+constexpr int kKsumFormTC = 6;   // ksum_variant value of the tensor-core form
+bool ksum_tc_supported(const mlb_ctx* ctx);
+bool ksum_tc_self(mlb_ctx* ctx, const double* a, double* out);
 // solve.cu: PCG on C~_W x = b (nwav vectors on the device)
 mlb_status pcg_run(mlb_ctx* ctx, const double* b, double* x, mlb_info* info);
 // kRhs simultaneous PCG solves on the FP32 panels (one pass over C~_W per iteration)

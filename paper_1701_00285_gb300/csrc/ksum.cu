@@ -20,6 +20,11 @@ mlb_status kernel_sum_general(mlb_ctx* ctx, const double* targets, int64_t M, co
     }
     const double* tg = targets ? targets : ctx->xs;
     if (!sources) Ns = ctx->N;
+    // the matrix-free product's sum of the data points against themselves:
+    // the tensor-core form when the autotuner chose it
+    if (ctx->ksum_variant == kKsumVariantTC && ctx->opts.precision == MLB_MIXED && !accurate && !deriv &&
+        !targets && !sources && !add_trend && M == ctx->N && ksum_tc_self(ctx, weights, out))
+        return MLB_OK;
     switch (ctx->d) {
 #define MLB_KSUM_CASE(DD)                                                                          \
     case DD:                                                                                       \
@@ -38,11 +43,13 @@ mlb_status kernel_sum_general(mlb_ctx* ctx, const double* targets, int64_t M, co
 }
 
 // Autotuner for the FP32 kernel sum of the matrix-free product: times every
-// launch shape once on the context's own points (CUDA events on its stream)
-// and keeps the fastest, cached per (device, dimension, problem-size bucket)
-// for the rest of the process.  Runs outside any stream capture.
+// launch shape, and the tensor-core form where the dimension and covariance
+// have one, once on the context's own points (CUDA events on its stream) and
+// keeps the fastest, cached per (device, dimension, covariance kind,
+// problem-size bucket) for the rest of the process.  Runs outside any stream
+// capture.
 static std::mutex g_tune_mutex;
-static std::map<std::tuple<int, int, int>, int> g_tune_cache;
+static std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
 
 mlb_status tune_kernel_sum(mlb_ctx* ctx) {
     ctx->ksum_variant = 1;
@@ -51,7 +58,7 @@ mlb_status tune_kernel_sum(mlb_ctx* ctx) {
     cudaGetDevice(&dev);
     int bucket = 0;
     while ((1LL << (bucket + 1)) <= ctx->N) ++bucket;
-    const auto key = std::make_tuple(dev, ctx->d, bucket);
+    const auto key = std::make_tuple(dev, ctx->d, ctx->kfn.kind, bucket);
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
@@ -68,7 +75,8 @@ mlb_status tune_kernel_sum(mlb_ctx* ctx) {
     cudaEventCreate(&e1);
     float best = 1e30f;
     int bestv = 1;
-    for (int v = 0; v < kKsumVariants; ++v) {
+    for (int v = 0; v <= kKsumVariantTC; ++v) {
+        if (v == kKsumVariantTC && !ksum_tc_supported(ctx)) continue;
         ctx->ksum_variant = v;
         mlb_status s = kernel_sum_general(ctx, nullptr, ctx->N, nullptr, ctx->N, a, b, false, false, false);
         if (s != MLB_OK) break;

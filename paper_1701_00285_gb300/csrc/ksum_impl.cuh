@@ -334,6 +334,8 @@ static void launch_reduce(mlb_ctx* ctx, const KsumSplit& sp, const double* tg, i
 // autotuner below picks one per device and dimension.  Every dimension has the
 // default (4 targets, 128 threads); the common ones have all six.
 constexpr int kKsumVariants = 6;
+constexpr int kKsumVariantTC = kKsumFormTC;     // the tensor-core form (ksum_tc.cu), self sums only
+static_assert(kKsumVariantTC == kKsumVariants, "the tensor-core form follows the launch shapes");
 constexpr int kVarTpt[kKsumVariants] = {2, 4, 8, 2, 4, 8};
 constexpr int kVarBs[kKsumVariants] = {128, 128, 128, 256, 256, 256};
 
