@@ -28,7 +28,8 @@ def main(argv=None) -> None:
     ap.add_argument("--leaf-size", type=int, default=None, help="default: the workload's leaf size")
     ap.add_argument("--matrix-free", action="store_true", help="d = 10 three-step product")
     ap.add_argument("--variant", type=int, default=None,
-                    help="symmetric FP32 product form (0 loads, 1 bulk copies); default: the autotuned one")
+                    help="product form: symmetric storage 0 loads, 1 bulk copies; matrix-free kernel sum 0..5 "
+                         "launch shapes, 6 tensor cores; default: the autotuned one")
     a = ap.parse_args(argv)
 
     import torch
@@ -44,7 +45,7 @@ def main(argv=None) -> None:
             c.set_stream(st.cuda_stream)
             c.build_basis(P.points, P.w)
             c.assemble(P.nu, P.rho, P.nugget, math.inf)
-            if a.variant is not None and prec == "mixed" and not a.matrix_free:
+            if a.variant is not None and prec == "mixed":
                 c.set_product_variant(a.variant)
             nw = c.nwav
             with torch.cuda.stream(st):
@@ -66,7 +67,7 @@ def main(argv=None) -> None:
                 # the kernel sum dominates: N^2 point pairs per product
                 pairs = a.n * a.n
                 print(json.dumps({"precision": prec, "n": a.n, "d": P.points.shape[1], "nwav": nw,
-                                  "matrix_free": True, "ms": ms, "pairs": pairs,
+                                  "matrix_free": True, "variant": c.info()["product_variant"], "ms": ms, "pairs": pairs,
                                   "pairs_per_s": pairs / (ms / 1000.0)}), flush=True)
             else:
                 vb = 4 if prec == "mixed" else 8

@@ -168,3 +168,47 @@ def test_high_dimension_regime_n32768(pkg):
     ref = (design.design_matrix(tg, P.w, lo, hi) @ out["fp64"]["beta"]
            + matern.kernel_matvec(tg, P.points, out["fp64"]["gamma"], P.nu, P.rho))
     assert rel(out["fp64"]["yhat"][:64], ref) < 1e-10
+
+
+@pytest.mark.parametrize("d", [10, 5])
+def test_tensor_core_kernel_sum_matches_fp64(pkg, d):
+    """The matrix-free product with its kernel sum on the tensor cores (squared
+    distances as one BF16x3 contraction, variant 6) against the FP64 product
+    and the FP32 CUDA-core form, on a ragged size (4,000 points: a partial last
+    target block and source tile) with the sources split over CTAs."""
+    P = wl.uniform_10d(N=4000, M=16) if d == 10 else wl.heldout_5d(N=4000, M=16)
+    leaf = 128 if d == 10 else 64
+    ref = pkg.Context("fp64", leaf_size=leaf, matrix_free=True, precond=False)
+    ref.build_basis(P.points, P.w)
+    ref.assemble(P.nu, P.rho, P.nugget, math.inf)
+    u = np.random.default_rng(31).standard_normal(ref.nwav)
+    want = ref.cw_matvec(u)
+    ref.close()
+    ctx = pkg.Context("mixed", leaf_size=leaf, matrix_free=True, precond=False)
+    ctx.build_basis(P.points, P.w)
+    ctx.assemble(P.nu, P.rho, P.nugget, math.inf)
+    errs = {}
+    for v in (1, 6):
+        ctx.set_product_variant(v)
+        assert ctx.info()["product_variant"] == v
+        got = ctx.cw_matvec(u)
+        assert np.all(np.isfinite(got))
+        errs[v] = rel(got, want)
+    ctx.close()
+    assert errs[1] < 1e-5
+    assert errs[6] < 1e-5, errs
+
+
+def test_tensor_core_product_blup_matches_dense_oracle(pkg):
+    """A mixed matrix-free BLUP whose every product runs on the tensor cores,
+    against the dense oracle (the mixed path's 1e-5)."""
+    P = wl.small_problem(650, 2000, 10, 1, nu=2.5, rho=0.8, nugget=1e-4, leaf_size=128, M=100)
+    ref = dense.dense_blup(P.points, P.Z, P.targets, 1, 2.5, 0.8, 1e-4)
+    ctx = pkg.Context("mixed", leaf_size=128, pcg_rtol=1e-12, pcg_maxit=50000, precond=False, matrix_free=True)
+    ctx.build_basis(P.points, 1)
+    ctx.assemble(2.5, 0.8, 1e-4, math.inf)
+    ctx.set_product_variant(6)
+    ctx.solve(P.Z)
+    got = ctx.predict(P.targets)
+    ctx.close()
+    assert rel(got, ref["yhat"]) < MIXED_TOL
