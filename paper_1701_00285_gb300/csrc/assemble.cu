@@ -750,11 +750,11 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
     MLB_CHECK_LAUNCH(ctx, "diag_kernel");
     // the SS / SW work matrices are no longer needed
     for (int l = 0; l <= t; ++l) {
-        dfree(A, SS[l]);
-        dfree(A, SW[l]);
+        dfree(ctx, A, SS[l]);
+        dfree(ctx, A, SW[l]);
     }
-    dfree(A, X0);
-    dfree(A, X1);
+    dfree(ctx, A, X0);
+    dfree(ctx, A, X1);
     if (mixed) {
         // complete pattern: each symmetric pair stored once in FP32 (symv.cu)
         bool complete = ctx->allow_sym && ctx->nwav > 0;
@@ -763,7 +763,7 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
         if (complete) {
             mlb_status ss = build_sym(ctx);
             if (ss != MLB_OK) return ss;
-            dfree(A, pan.vals);
+            dfree(ctx, A, pan.vals);
             pan.vals = nullptr;
             return MLB_OK;
         }
@@ -807,7 +807,7 @@ mlb_status assemble_dev(mlb_ctx* ctx) {
         to_f32_kernel<<<1216, 256, 0, st>>>(pan.vals, std::max<int64_t>(1, stored), pan.vals32);
         MLB_CHECK_LAUNCH(ctx, "to_f32_kernel");
         MLB_CUDA(ctx, cudaStreamSynchronize(st));
-        dfree(A, pan.vals);
+        dfree(ctx, A, pan.vals);
         pan.vals = nullptr;
     }
     return MLB_OK;

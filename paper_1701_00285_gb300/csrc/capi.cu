@@ -46,10 +46,11 @@ mlb_status allow_max_dynamic_smem(mlb_ctx* ctx, const void* func, const char* na
     return e == cudaSuccess ? MLB_OK : cuda_fail(ctx, e, name);
 }
 
-void dfree(Arena& a, void* p) {
+void dfree(mlb_ctx* ctx, Arena& a, void* p) {
     if (!p) return;
     for (size_t i = 0; i < a.ptrs.size(); ++i)
         if (a.ptrs[i] == p) {
+            cudaStreamSynchronize(ctx->stream);
             cudaFree(p);
             a.ptrs.erase(a.ptrs.begin() + i);
             return;
@@ -159,6 +160,7 @@ mlb_status host_roundtrip(mlb_ctx* ctx, const double* in, int64_t nin, double* o
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) s = cuda_fail(ctx, e, "copy back");
     }
+    cudaStreamSynchronize(ctx->stream);   // an error path may leave work queued on the buffers
     cudaFree(din);
     cudaFree(dout);
     return s;
@@ -600,6 +602,7 @@ mlb_status mlb_predict(mlb_ctx* ctx, const double* targets, int64_t M, double* y
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) s = cuda_fail(ctx, e, "predict");
     }
+    cudaStreamSynchronize(ctx->stream);
     cudaFree(tg);
     cudaFree(y);
     return s;
@@ -658,9 +661,11 @@ mlb_status mlb_cw_matvec(mlb_ctx* ctx, const double* u, double* out) {
     if (s == MLB_OK && ctx->sym.err) {
         // the product's bounded waits report here (host_roundtrip has synchronised)
         int e = 0;
-        MLB_CUDA(ctx, cudaMemcpy(&e, ctx->sym.err, sizeof(int), cudaMemcpyDeviceToHost));
+        MLB_CUDA(ctx, cudaMemcpyAsync(&e, ctx->sym.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        MLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         if (e) {
-            MLB_CUDA(ctx, cudaMemset(ctx->sym.err, 0, sizeof(int)));
+            MLB_CUDA(ctx, cudaMemsetAsync(ctx->sym.err, 0, sizeof(int), ctx->stream));
+            MLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
             return fail(ctx, MLB_ETIMEOUT, "a bounded wait of the matrix product gave up");
         }
     }
@@ -723,8 +728,9 @@ mlb_status mlb_get_pattern(mlb_ctx* ctx, int i, int j, uint8_t* flags) {
     std::vector<int> row(nj);
     for (int m = 0; m < ni; ++m) {
         const int64_t gm = ni - 1 + m;
-        MLB_CUDA(ctx, cudaMemcpy(row.data(), ctx->pan.bcol + gm * ctx->ncell + (nj - 1), sizeof(int) * nj,
-                                 cudaMemcpyDeviceToHost));
+        MLB_CUDA(ctx, cudaMemcpyAsync(row.data(), ctx->pan.bcol + gm * ctx->ncell + (nj - 1), sizeof(int) * nj,
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+        MLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         for (int q = 0; q < nj; ++q) flags[(int64_t)m * nj + q] = row[q] >= 0 ? 1 : 0;
     }
     return MLB_OK;
@@ -769,6 +775,7 @@ mlb_status mlb_mse(mlb_ctx* ctx, const double* targets, int64_t M, double* mse_o
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) s = cuda_fail(ctx, e, "MSE copy");
     }
+    cudaStreamSynchronize(ctx->stream);
     cudaFree(tg);
     cudaFree(o);
     return s;
@@ -795,6 +802,7 @@ mlb_status mlb_grad(mlb_ctx* ctx, const double* targets, int64_t M, const double
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) s = cuda_fail(ctx, e, "gradient copy");
     }
+    cudaStreamSynchronize(ctx->stream);
     cudaFree(tg);
     cudaFree(y);
     cudaFree(o3);

@@ -138,6 +138,8 @@ struct PcgState {
     unsigned ticket;     // CTAs of the current launch that have finished (last-CTA reductions)
 };
 
+// Device allocations of one lifetime.  release() frees them all; callers
+// synchronise every stream that uses them first (cudaFree need not wait).
 struct Arena {
     std::vector<void*> ptrs;
     void release();
@@ -216,7 +218,12 @@ namespace mlb {
 mlb_status fail(mlb_ctx* ctx, mlb_status s, const std::string& msg);
 mlb_status cuda_fail(mlb_ctx* ctx, cudaError_t e, const char* where);
 void* dalloc(mlb_ctx* ctx, Arena& a, size_t bytes);
-void dfree(Arena& a, void* p);
+// Frees one allocation of the arena after the context's stream has drained:
+// cudaFree is documented only as possibly synchronising, and kernels queued
+// on the stream may still write the buffer.  Freed memory goes straight back
+// to the device allocator, where another host thread's cudaMalloc can take it
+// for work on another stream.
+void dfree(mlb_ctx* ctx, Arena& a, void* p);
 // largest dynamic shared memory a block may opt in to on the current device
 int max_smem_optin();
 // opts a kernel in to all the dynamic shared memory its static share leaves free;

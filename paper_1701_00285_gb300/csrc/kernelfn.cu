@@ -172,8 +172,14 @@ mlb_status setup_kernel_fn(mlb_ctx* ctx) {
         double* tab = (double*)dalloc(ctx, A, sizeof(double) * T->c.size());
         float* tab32 = (float*)dalloc(ctx, A, sizeof(float) * c32.size());
         if (!tab || !tab32) return fail(ctx, MLB_ENOMEM, "covariance table");
-        MLB_CUDA(ctx, cudaMemcpy(tab, T->c.data(), sizeof(double) * T->c.size(), cudaMemcpyHostToDevice));
-        MLB_CUDA(ctx, cudaMemcpy(tab32, c32.data(), sizeof(float) * c32.size(), cudaMemcpyHostToDevice));
+        // on the context's stream: a plain cudaMemcpy from pageable memory may
+        // return before its DMA lands, and the legacy stream it runs on is not
+        // ordered with the context's non-blocking stream
+        MLB_CUDA(ctx, cudaMemcpyAsync(tab, T->c.data(), sizeof(double) * T->c.size(), cudaMemcpyHostToDevice,
+                                      ctx->stream));
+        MLB_CUDA(ctx, cudaMemcpyAsync(tab32, c32.data(), sizeof(float) * c32.size(), cudaMemcpyHostToDevice,
+                                      ctx->stream));
+        MLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         K.tab = tab;
         K.tab32 = tab32;
         K.noct = T->noct;

@@ -454,7 +454,7 @@ mlb_status sym_reserve(mlb_ctx* ctx, int nrhs) {
     if (nrhs <= S.nrhs && S.nsegMax <= S.nsegCap) return MLB_OK;
     nrhs = std::max(nrhs, S.nrhs);
     Arena& A = ctx->arena_asm;
-    for (void* q : {(void*)S.rowpart, (void*)S.colpart, (void*)S.xh, (void*)S.xl}) dfree(A, q);
+    for (void* q : {(void*)S.rowpart, (void*)S.colpart, (void*)S.xh, (void*)S.xl}) dfree(ctx, A, q);
     S.rowpart = S.colpart = nullptr;
     S.xh = S.xl = nullptr;
     S.nrhs = 0;
@@ -497,7 +497,7 @@ static mlb_status sym_plan(mlb_ctx* ctx, int seg) {
     if (work.size() > max_work_items(ctx->ncell, ctx->N)) return fail(ctx, MLB_EINVAL, "symmetric work table bound");
     Arena& A = ctx->arena_asm;
     if (!S.work || (int)work.size() > S.nworkCap) {
-        dfree(A, S.work);
+        dfree(ctx, A, S.work);
         S.work = (int2*)dalloc(ctx, A, sizeof(int2) * work.size());
         if (!S.work) return fail(ctx, MLB_ENOMEM, "symmetric work table");
         S.nworkCap = (int)work.size();
