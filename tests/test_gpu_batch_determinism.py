@@ -15,6 +15,13 @@ import workloads as wl
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1701_00285_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_batch_repeats_bit_identical(pkg, prec):
     from paper_1701_00285_gb300.binding import batch_solve, lib
