@@ -429,11 +429,14 @@ def extra_matrix_free_product(pkg, torch, stream, local_rank):
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    variant = ctx.info()["product_variant"]     # the autotuner's choice for this size
     ctx.close()
     flops = float(P.N) * P.N * ksum_flops_per_pair(P.d)
     achieved = flops / (ms / 1000.0) / 1e12
+    kernel = "ksum_tc_kernel" if variant == 6 else "ksum_f32_kernel"
     return {"workload": describe(P), "ms_per_product": ms, "pairs_per_s": float(P.N) * P.N / (ms / 1000.0),
-            "roofline": {"kernel": "ksum_f32_kernel", "bound": "alu", "achieved": achieved,
+            "product_variant": variant,
+            "roofline": {"kernel": kernel, "bound": "alu", "achieved": achieved,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                          "peak_source": "nominal", "algorithmic_flops": flops}}
 
@@ -524,6 +527,7 @@ def run_batched(args, rank, world, local_rank):
             "e2e": {"value": value, "unit": "BLUP solves/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": out["mixed"]["launches"],
+            "launches_per_problem": out["mixed"]["launches"] / (args.steps * args.count),
             "phases_ms": out["mixed"]["phases"],
             "fp64": {"value": world * args.count * args.steps / out["fp64"]["s"],
                      "ms_per_step": 1000 * out["fp64"]["s"] / args.steps, "phases_ms": out["fp64"]["phases"]},

@@ -166,7 +166,10 @@ __global__ void __launch_bounds__(128) qr_level_kernel(CellTables C, const doubl
     if (tid == 0) {
         double dmin = DBL_MAX;
         for (int i = 0; i < a; ++i) dmin = fmin(dmin, fabs(A[i * p + i]));
-        if (a > 0 && dmin <= 10.0 * (double)max(p, s) * DBL_EPSILON * normF) atomicOr(flag, 1);
+        if (a > 0 && dmin <= 10.0 * (double)max(p, s) * DBL_EPSILON * normF) {
+            atomicOr(flag, 1);
+            atomicMax(flag + 1, g + 1);     // the highest failing cell, for the error message
+        }
     }
     // Q = H_0 H_1 ... H_{m-1}, accumulated backwards on the identity
     double* Q = V + C.vOff[g];

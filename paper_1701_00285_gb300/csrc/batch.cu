@@ -7,12 +7,16 @@
 // single-problem kernels on a pool of streams driven by host threads.  The PCG
 // phase, where a per-problem loop would be bound by kernel launches (five
 // launches per iteration on systems of a few thousand unknowns), is one
-// persistent launch: one CTA per problem runs its whole diagonally
-// preconditioned CG (Sec. 5.2 remark, Sec. 6.2) with block-level reductions
-// only -- no CTA waits for another.  Problems with more than kCtaRows
-// unknowns would hold one SM for many iterations of a product that wants
-// the whole GPU; they run the single-problem PCG (full-grid product, CUDA
-// graph chunks) on the stream pool while the persistent launch runs.
+// persistent launch over all problems: each problem's diagonally
+// preconditioned CG (Sec. 5.2 remark, Sec. 6.2) is a chain of phases (the
+// product q = C~_W p, the update of x, r, z), each phase cut into row chunks
+// that any CTA may take.  The CTA finishing a phase's last chunk reduces the
+// chunks' partial sums in chunk order and opens the next phase, so the
+// result does not depend on which CTA did what, and no CTA waits for
+// another: CTAs without work take chunks of other problems.  A long-running
+// problem therefore gets the whole GPU once the others are done.  Systems
+// too wide to stage their search direction in shared memory run the
+// single-problem PCG on the stream pool meanwhile.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -22,15 +26,27 @@
 #include <vector>
 
 #include "internal.h"
+#include "bulk.cuh"
+#include "pcg_device.cuh"
 
 namespace mlb {
 
-// largest system solved by one CTA of the persistent launch
-constexpr int kCtaRows = 1024;
+// The persistent PCG takes systems of at most kFlowCols unknowns: every
+// chunk of a product stages the search direction in shared memory, 8 bytes
+// per column.
+constexpr int kFlowCols = 12288;
+constexpr int kFlowThreads = 256;
+constexpr int kFlowWarps = kFlowThreads / 32;
+constexpr int kUpdRows = 1024;                 // rows per chunk of the vector phases
+constexpr int kFlowDenseRows = 32;             // rows per product chunk, complete patterns (4 per warp)
+constexpr int64_t kProdValues = 1 << 18;       // panel values per product chunk, truncated patterns
+constexpr int kFlowSpan = 2048;                // columns summed in FP32 before the FP64 sum
 
-struct BatchPcgProblem {
-    const double* vals64;      // panel values (FP64 path) or nullptr
+// One problem of the persistent launch: its panels (row panels of C~_W, FP32
+// or FP64), its vectors and the chunking of its phases.
+struct FlowProblem {
     const float* vals32;       // panel values (mixed path) or nullptr
+    const double* vals64;      // panel values (FP64 path) or nullptr
     const int* colidx;
     const int* ncols;
     const int64_t* valOff;
@@ -42,144 +58,469 @@ struct BatchPcgProblem {
     double* x;
     double* r;
     double* z;
-    double* p;
+    double* p0;                // search directions of even iterations
+    double* p1;                // and of odd ones
     double* q;
-    int64_t n;
-    double tol2;
-    int maxit;
-    int pad;
+    double* part;              // per chunk of the current phase: its partial sums
     PcgState* st;
+    double tol2;
+    int n;
+    int width;                 // staged columns: n rounded up to the panels' padding
+    int dense;                 // every panel holds all n columns in order (no index lists)
+    int prodRows;              // rows per product chunk
+    int nprod, nupd;           // chunks of a product phase and of a vector phase
+    int maxit;
 };
 
-__device__ double cta_sum(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// Scheduling state of one problem.  Phases are numbered by epoch: 0 sets up
+// the residual, 2i + 1 is the product of iteration i, 2i + 2 its update.
+// `ticket` hands out the chunks of the current epoch (epoch << 32 | next
+// chunk); the CTA that finishes the epoch's last chunk reduces the partial
+// sums, sets the scalars and opens the next epoch.  No CTA ever waits for
+// another one: a CTA without work looks at other problems.
+struct FlowCtl {
+    unsigned long long ticket;
+    unsigned done;             // chunks of the current epoch finished
+    int finished;
+    double rz, bb, rr, alpha, beta;
+    int it;
+};
+
+struct FlowGlobal {
+    int remaining;             // problems not finished
+    unsigned progress;         // epochs opened or problems finished, all problems
+    int err;                   // set when no problem made progress for kWaitCycles
+};
+
+__device__ __forceinline__ unsigned flow_chunks(const FlowProblem& P, unsigned e) {
+    return (e & 1u) ? (unsigned)P.nprod : (unsigned)P.nupd;
+}
+
+__device__ __forceinline__ double* flow_dir(const FlowProblem& P, int it) { return (it & 1) ? P.p1 : P.p0; }
+
+// Fixed-order CTA sum of two values (all threads get both).
+__device__ __forceinline__ double2 flow_sum2(double a, double b, double* red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    double s = 0.0;
-    const int nw = blockDim.x >> 5;
-    for (int i = 0; i < nw; ++i) s += red[i];
-    return s;
-}
-
-// q = A p by warp-per-row over the problem's panels; returns p.q (all
-// threads).  p is staged in shared memory first (n <= kCtaRows), so the
-// column gather reads shared memory and only the values and column indices
-// stream from global memory, four at a time (panel rows start 16-byte
-// aligned and hold a multiple of 4 columns).
-__device__ double cta_spmv(const BatchPcgProblem& P, const double* __restrict__ pv, double* __restrict__ q,
-                           double* xs, double* red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t i = threadIdx.x; i < P.n; i += blockDim.x) xs[i] = pv[i];
-    __syncthreads();
-    double dot = 0.0;
-    for (int64_t r = warp; r < P.n; r += nw) {
-        const int g = P.rowCell[r];
-        const int64_t i = r - P.wOff[g];
-        const int n = P.ncols[g];
-        const int* ci = P.colidx + P.colOff[g];
-        double acc = 0.0;
-        if (P.vals32) {
-            // four 16-byte value and index loads per lane in flight before any is used
-            const float* v = P.vals32 + P.valOff[g] + i * n;
-            for (int j0 = 4 * lane; j0 < n; j0 += 512) {
-                float4 a[4];
-                int4 c[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + 128 * u;
-                    if (j < n) {
-                        a[u] = *reinterpret_cast<const float4*>(v + j);
-                        c[u] = *reinterpret_cast<const int4*>(ci + j);
-                    } else {
-                        a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        c[u] = make_int4(0, 0, 0, 0);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    acc += (double)a[u].x * xs[c[u].x] + (double)a[u].y * xs[c[u].y] + (double)a[u].z * xs[c[u].z] +
-                           (double)a[u].w * xs[c[u].w];
-            }
-        } else {
-            const double* v = P.vals64 + P.valOff[g] + i * n;
-            for (int j = 4 * lane; j < n; j += 128) {
-                const double2 a = *reinterpret_cast<const double2*>(v + j);
-                const double2 b = *reinterpret_cast<const double2*>(v + j + 2);
-                const int4 c = *reinterpret_cast<const int4*>(ci + j);
-                acc += a.x * xs[c.x] + a.y * xs[c.y] + b.x * xs[c.z] + b.y * xs[c.w];
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-            q[r] = acc;
-            dot += xs[r] * acc;
-        }
+    if (lane == 0) {
+        red[wid] = a;
+        red[kFlowWarps + wid] = b;
     }
-    return cta_sum(dot, red);
+    __syncthreads();
+    double sa = 0.0, sb = 0.0;
+    for (int i = 0; i < kFlowWarps; ++i) {
+        sa += red[i];
+        sb += red[kFlowWarps + i];
+    }
+    return make_double2(sa, sb);
 }
 
-// One CTA per problem; the iteration matches pcg_run: x0 = 0, stop when
-// ||r_k||^2 <= tol^2 ||b||^2 on the recursive unpreconditioned residual.
-__global__ void __launch_bounds__(512) batch_pcg_kernel(const BatchPcgProblem* __restrict__ probs) {
-    __shared__ double red[32];
-    __shared__ double xs[kCtaRows];
-    const BatchPcgProblem P = probs[blockIdx.x];
-    const int64_t n = P.n;
+// Epoch 0, rows [r0, r1): x = 0, r = b, z = D^-1 b, p_0 = z; partials b.z, b.b.
+__device__ void flow_init(const FlowProblem& P, int c, double* red) {
+    const int r0 = c * kUpdRows, r1 = min(P.n, r0 + kUpdRows);
     double rz = 0.0, bb = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = r0 + threadIdx.x; i < r1; i += kFlowThreads) {
         const double bi = P.b[i];
         const double zi = P.diag ? bi / P.diag[i] : bi;
         P.x[i] = 0.0;
         P.r[i] = bi;
         P.z[i] = zi;
-        P.p[i] = zi;
+        P.p0[i] = zi;
         rz += bi * zi;
         bb += bi * bi;
     }
-    rz = cta_sum(rz, red);
-    bb = cta_sum(bb, red);
-    int it = 0, status = 0;
-    double rr = bb;
-    if (bb > 0.0) {
-        while (true) {
-            __syncthreads();
-            const double pq = cta_spmv(P, P.p, P.q, xs, red);
-            if (!(pq > 0.0)) {
-                status = 1;
-                break;
-            }
-            const double alpha = rz / pq;
-            double rrl = 0.0, rzl = 0.0;
-            for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-                P.x[i] += alpha * P.p[i];
-                const double ri = P.r[i] - alpha * P.q[i];
-                P.r[i] = ri;
-                const double zi = P.diag ? ri / P.diag[i] : ri;
-                P.z[i] = zi;
-                rrl += ri * ri;
-                rzl += ri * zi;
-            }
-            rr = cta_sum(rrl, red);
-            const double rzn = cta_sum(rzl, red);
-            ++it;
-            if (rr <= P.tol2 * bb) break;
-            if (it >= P.maxit) {
-                status = 2;
-                break;
-            }
-            const double beta = rzn / rz;
-            rz = rzn;
-            for (int64_t i = threadIdx.x; i < n; i += blockDim.x) P.p[i] = P.z[i] + beta * P.p[i];
+    const double2 s = flow_sum2(rz, bb, red);
+    if (threadIdx.x == 0) {
+        P.part[2 * c] = s.x;
+        P.part[2 * c + 1] = s.y;
+    }
+}
+
+// Epoch 2i + 1, rows [r0, r1): p_i = z + beta p_(i-1) (p_0 as set up), staged
+// in shared memory (FP32 high and low parts for FP32 panels), q = C~_W p_i on
+// the chunk's rows, warp per row; partial p_i.q.  FP32 values are summed in
+// FP32 over each lane's 16 values of a 512-column step, the steps in FP64.
+__device__ void flow_product(const FlowProblem& P, int it, double beta, int c, double* red, double* vstage) {
+    const int r0 = c * P.prodRows, r1 = min(P.n, r0 + P.prodRows);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int w = P.width;
+    double* pnew = flow_dir(P, it);
+    const double* pold = flow_dir(P, it + 1);     // p_(i-1): the other buffer
+    const bool mixed = P.vals32 != nullptr;
+    float* vh = reinterpret_cast<float*>(vstage);
+    float* vl = vh + w;
+    // pull this chunk's panel rows towards L2 while the direction is staged
+    // (rows of one cell are contiguous; each row starts 16-byte aligned and
+    // holds a multiple of 16 bytes)
+    for (int row = r0 + threadIdx.x; row < r1; row += kFlowThreads) {
+        const int g = P.rowCell[row];
+        const int nc = P.ncols[g];
+        const int64_t off = P.valOff[g] + (int64_t)(row - P.wOff[g]) * nc;
+        const char* src = mixed ? (const char*)(P.vals32 + off) : (const char*)(P.vals64 + off);
+        const unsigned bytes = (unsigned)nc * (mixed ? 4u : 8u);
+        for (unsigned o = 0; o < bytes; o += 32768u)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src + o), "r"(min(32768u, bytes - o))
+                         : "memory");
+    }
+    for (int j = threadIdx.x; j < w; j += kFlowThreads) {
+        double v = 0.0;
+        if (j < P.n) v = it == 0 ? __ldcg(P.p0 + j) : __ldcg(P.z + j) + beta * __ldcg(pold + j);
+        if (mixed) {
+            const float h = (float)v;
+            vh[j] = h;
+            vl[j] = (float)(v - (double)h);
+        } else {
+            vstage[j] = v;
         }
     }
+    if (it > 0)
+        for (int row = r0 + threadIdx.x; row < r1; row += kFlowThreads)
+            pnew[row] = __ldcg(P.z + row) + beta * __ldcg(pold + row);
+    __syncthreads();
+    double pq = 0.0;
+    if (P.dense) {
+        // every row holds all w columns in order: four rows per warp share
+        // each staged column load; FP32 sums over blocks of kFlowSpan
+        // columns, FP64 across blocks
+        for (int rg = r0 + 4 * warp; rg < r1; rg += 4 * kFlowWarps) {
+            const void* rowp[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = min(rg + q, r1 - 1);
+                const int g = P.rowCell[row];
+                const int64_t off = P.valOff[g] + (int64_t)(row - P.wOff[g]) * w;
+                rowp[q] = mixed ? (const void*)(P.vals32 + off) : (const void*)(P.vals64 + off);
+            }
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int jb = 0; jb < w; jb += kFlowSpan) {
+                const int je = min(w, jb + kFlowSpan);
+                if (mixed) {
+                    float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int j0 = jb + 4 * lane; j0 < je; j0 += 256) {
+                        const int j1 = j0 + 128;
+                        const bool ok1 = j1 < je;
+                        float4 a0[4], a1[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float* rp = reinterpret_cast<const float*>(rowp[q]);
+                            a0[q] = __ldg(reinterpret_cast<const float4*>(rp + j0));
+                            a1[q] = ok1 ? __ldg(reinterpret_cast<const float4*>(rp + j1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                        const float4 h0 = *reinterpret_cast<const float4*>(vh + j0);
+                        const float4 l0 = *reinterpret_cast<const float4*>(vl + j0);
+                        const float4 h1 = ok1 ? *reinterpret_cast<const float4*>(vh + j1) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 l1 = ok1 ? *reinterpret_cast<const float4*>(vl + j1) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float t = sh[q];
+                            t = fmaf(a0[q].x, h0.x, t); t = fmaf(a0[q].y, h0.y, t); t = fmaf(a0[q].z, h0.z, t); t = fmaf(a0[q].w, h0.w, t);
+                            t = fmaf(a1[q].x, h1.x, t); t = fmaf(a1[q].y, h1.y, t); t = fmaf(a1[q].z, h1.z, t); t = fmaf(a1[q].w, h1.w, t);
+                            sh[q] = t;
+                            float u = sl[q];
+                            u = fmaf(a0[q].x, l0.x, u); u = fmaf(a0[q].y, l0.y, u); u = fmaf(a0[q].z, l0.z, u); u = fmaf(a0[q].w, l0.w, u);
+                            u = fmaf(a1[q].x, l1.x, u); u = fmaf(a1[q].y, l1.y, u); u = fmaf(a1[q].z, l1.z, u); u = fmaf(a1[q].w, l1.w, u);
+                            sl[q] = u;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] += (double)sh[q] + (double)sl[q];
+                } else {
+                    for (int j0 = jb + 4 * lane; j0 < je; j0 += 128) {
+                        double2 a0[4], a1[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const double* rp = reinterpret_cast<const double*>(rowp[q]);
+                            a0[q] = __ldg(reinterpret_cast<const double2*>(rp + j0));
+                            a1[q] = __ldg(reinterpret_cast<const double2*>(rp + j0 + 2));
+                        }
+                        const double2 v0 = *reinterpret_cast<const double2*>(vstage + j0);
+                        const double2 v1 = *reinterpret_cast<const double2*>(vstage + j0 + 2);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            acc[q] += a0[q].x * v0.x + a0[q].y * v0.y + a1[q].x * v1.x + a1[q].y * v1.y;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double a = acc[q];
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                const int row = rg + q;
+                if (lane == 0 && row < r1) {
+                    P.q[row] = a;
+                    const double prow = it == 0 ? __ldcg(P.p0 + row) : __ldcg(P.z + row) + beta * __ldcg(pold + row);
+                    pq += prow * a;
+                }
+            }
+        }
+    } else {
+    for (int row = r0 + warp; row < r1; row += kFlowWarps) {
+        const int g = P.rowCell[row];
+        const int nc = P.ncols[g];
+        const int64_t off = P.valOff[g] + (int64_t)(row - P.wOff[g]) * nc;
+        const int* ci = P.colidx + P.colOff[g];
+        double acc = 0.0;
+        if (mixed) {
+            const float* a = P.vals32 + off;
+            for (int j0 = 4 * lane; j0 < nc; j0 += 512) {
+                float4 v[4];
+                int4 cc[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + 128 * u;
+                    v[u] = j < nc ? __ldg(reinterpret_cast<const float4*>(a + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    cc[u] = (P.dense || j >= nc) ? make_int4(j, j + 1, j + 2, j + 3)
+                                                 : __ldg(reinterpret_cast<const int4*>(ci + j));
+                }
+                float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (j0 + 128 * u >= nc) break;
+                    sh = fmaf(v[u].x, vh[cc[u].x], sh);
+                    sh = fmaf(v[u].y, vh[cc[u].y], sh);
+                    sh = fmaf(v[u].z, vh[cc[u].z], sh);
+                    sh = fmaf(v[u].w, vh[cc[u].w], sh);
+                    sl = fmaf(v[u].x, vl[cc[u].x], sl);
+                    sl = fmaf(v[u].y, vl[cc[u].y], sl);
+                    sl = fmaf(v[u].z, vl[cc[u].z], sl);
+                    sl = fmaf(v[u].w, vl[cc[u].w], sl);
+                }
+                acc += (double)sh + (double)sl;
+            }
+        } else {
+            const double* a = P.vals64 + off;
+            for (int j = 4 * lane; j < nc; j += 128) {
+                const double2 a0 = __ldg(reinterpret_cast<const double2*>(a + j));
+                const double2 a1 = __ldg(reinterpret_cast<const double2*>(a + j + 2));
+                const int4 cc = P.dense ? make_int4(j, j + 1, j + 2, j + 3) : __ldg(reinterpret_cast<const int4*>(ci + j));
+                acc += a0.x * vstage[cc.x] + a0.y * vstage[cc.y] + a1.x * vstage[cc.z] + a1.y * vstage[cc.w];
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            P.q[row] = acc;
+            const double prow = it == 0 ? __ldcg(P.p0 + row) : __ldcg(P.z + row) + beta * __ldcg(pold + row);
+            pq += prow * acc;
+        }
+    }
+    }
+    const double2 s = flow_sum2(pq, 0.0, red);
+    if (threadIdx.x == 0) P.part[c] = s.x;
+}
+
+// Epoch 2i + 2, rows [r0, r1): x += alpha p_i, r -= alpha q, z = D^-1 r;
+// partials r.r and r.z.
+__device__ void flow_update(const FlowProblem& P, int it, double alpha, int c, double* red) {
+    const int r0 = c * kUpdRows, r1 = min(P.n, r0 + kUpdRows);
+    const double* p = flow_dir(P, it);
+    double rr = 0.0, rz = 0.0;
+    for (int i = r0 + threadIdx.x; i < r1; i += kFlowThreads) {
+        P.x[i] = __ldcg(P.x + i) + alpha * __ldcg(p + i);
+        const double ri = __ldcg(P.r + i) - alpha * __ldcg(P.q + i);
+        P.r[i] = ri;
+        const double zi = P.diag ? ri / P.diag[i] : ri;
+        P.z[i] = zi;
+        rr += ri * ri;
+        rz += ri * zi;
+    }
+    const double2 s = flow_sum2(rr, rz, red);
     if (threadIdx.x == 0) {
-        P.st->it = it;
-        P.st->rr = rr;
-        P.st->bb = bb;
-        P.st->status = status;
-        P.st->done = 1;
+        P.part[2 * c] = s.x;
+        P.part[2 * c + 1] = s.y;
+    }
+}
+
+// Warp 0: the chunks' partial sums in chunk order (pairs when `pairs`).
+__device__ __forceinline__ double2 flow_gather(const double* part, int nchunk, bool pairs) {
+    const int lane = threadIdx.x & 31;
+    double a = 0.0, b = 0.0;
+    for (int c = lane; c < nchunk; c += 32) {
+        if (pairs) {
+            a += __ldcg(part + 2 * c);
+            b += __ldcg(part + 2 * c + 1);
+        } else {
+            a += __ldcg(part + c);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    return make_double2(a, b);
+}
+
+__device__ void flow_open(FlowCtl& C, FlowGlobal* g, unsigned e) {
+    atomicExch(&C.done, 0u);
+    __threadfence();
+    atomicExch(&C.ticket, (unsigned long long)e << 32);
+    atomicAdd(&g->progress, 1u);
+}
+
+__device__ void flow_finish(const FlowProblem& P, FlowCtl& C, FlowGlobal* g, int it, double rr, int status) {
+    P.st->it = it;
+    P.st->rr = rr;
+    P.st->bb = C.bb;
+    P.st->status = status;
+    __threadfence();
+    P.st->done = 1;
+    atomicExch(&C.finished, 1);
+    atomicSub(&g->remaining, 1);
+    atomicAdd(&g->progress, 1u);
+}
+
+// The last finisher of epoch e: reduce, test, set the scalars, open e + 1.
+// Run by warp 0; lane 0 writes.  Matches pcg_run: x0 = 0, stop when
+// ||r_k||^2 <= tol^2 ||b||^2 on the recursive unpreconditioned residual.
+__device__ void flow_transition(const FlowProblem& P, FlowCtl& C, FlowGlobal* g, unsigned e) {
+    const int lane = threadIdx.x & 31;
+    if (e == 0) {
+        const double2 s = flow_gather(P.part, P.nupd, true);
+        if (lane == 0) {
+            C.rz = s.x;
+            C.bb = s.y;
+            C.rr = s.y;
+            C.it = 0;
+            C.beta = 0.0;
+            if (!(s.y > 0.0)) flow_finish(P, C, g, 0, s.y, ST_OK);
+            else flow_open(C, g, 1u);
+        }
+    } else if (e & 1u) {
+        const double2 s = flow_gather(P.part, P.nprod, false);
+        if (lane == 0) {
+            const int it = (int)((e - 1u) >> 1);
+            if (!(s.x > 0.0)) {
+                flow_finish(P, C, g, it, C.rr, ST_BREAKDOWN);
+            } else {
+                C.alpha = C.rz / s.x;
+                flow_open(C, g, e + 1u);
+            }
+        }
+    } else {
+        const double2 s = flow_gather(P.part, P.nupd, true);
+        if (lane == 0) {
+            const int it = (int)(e >> 1);           // iterations completed
+            C.rr = s.x;
+            C.it = it;
+            if (s.x <= P.tol2 * C.bb) {
+                flow_finish(P, C, g, it, s.x, ST_OK);
+            } else if (it >= P.maxit) {
+                flow_finish(P, C, g, it, s.x, ST_NOCONV);
+            } else {
+                C.beta = s.y / C.rz;
+                C.rz = s.y;
+                flow_open(C, g, e + 1u);
+            }
+        }
+    }
+}
+
+// All problems' PCGs in one launch.  Each CTA starts at its home problem
+// (CTAs spread over the problems in proportion to their panel sizes), takes
+// chunks of whatever epoch is open there, and moves on to other problems
+// when none is left.  Waiting happens only while no chunk is open anywhere;
+// if nothing moves for kWaitCycles the CTA sets g->err and leaves.
+__global__ void __launch_bounds__(kFlowThreads, 3) batch_flow_pcg_kernel(const FlowProblem* __restrict__ probs,
+                                                                      FlowCtl* ctl, int count,
+                                                                      const int* __restrict__ home, FlowGlobal* g) {
+    extern __shared__ __align__(16) double vstage[];
+    __shared__ double red[2 * kFlowWarps];
+    __shared__ int s_k, s_exit, s_last;
+    __shared__ unsigned s_chunk, s_epoch;
+    __shared__ double s_scalar;
+    const int lane = threadIdx.x & 31;
+    int cur = home[blockIdx.x];
+    bool idle = false;
+    unsigned seen = 0;
+    long long idle0 = 0;
+    while (true) {
+        if (threadIdx.x < 32) {
+            int k = -1;
+            unsigned chunk = 0, epoch = 0;
+            for (int base = 0; base < count && k < 0; base += 32) {
+                const int j = base + lane;
+                bool cand = false;
+                if (j < count) {
+                    const int kk = (cur + j) % count;
+                    if (!*(volatile int*)&ctl[kk].finished) {
+                        const unsigned long long t = *(volatile unsigned long long*)&ctl[kk].ticket;
+                        cand = (unsigned)t < flow_chunks(probs[kk], (unsigned)(t >> 32));
+                    }
+                }
+                unsigned m = __ballot_sync(0xffffffffu, cand);
+                while (m && k < 0) {
+                    const int l = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int kk = (cur + base + l) % count;
+                    int got = 0;
+                    if (lane == 0) {
+                        const unsigned long long t = atomicAdd(&ctl[kk].ticket, 1ull);
+                        epoch = (unsigned)(t >> 32);
+                        chunk = (unsigned)t;
+                        got = chunk < flow_chunks(probs[kk], epoch);
+                    }
+                    if (__shfl_sync(0xffffffffu, got, 0)) k = kk;
+                }
+            }
+            if (k >= 0) cur = k;      // k is the same in every lane, so cur stays warp-uniform
+            if (lane == 0) {
+                int ex = 0;
+                if (k >= 0) {
+                    idle = false;
+                } else if (*(volatile int*)&g->remaining <= 0 || *(volatile int*)&g->err) {
+                    ex = 1;
+                } else {
+                    const unsigned pr = *(volatile unsigned*)&g->progress;
+                    const long long now = clock64();
+                    if (!idle || pr != seen) {
+                        idle = true;
+                        seen = pr;
+                        idle0 = now;
+                    } else if (now - idle0 > kWaitCycles) {
+                        atomicExch(&g->err, 1);
+                        ex = 1;
+                    }
+                    __nanosleep(256);
+                }
+                s_k = k;
+                s_chunk = chunk;
+                s_epoch = epoch;
+                s_exit = ex;
+                if (k >= 0) {
+                    __threadfence();
+                    const FlowCtl& C = ctl[k];
+                    s_scalar = (epoch & 1u) ? __ldcg(&C.beta) : __ldcg(&C.alpha);
+                }
+            }
+        }
+        __syncthreads();
+        if (s_exit) break;
+        const int k = s_k;
+        if (k < 0) {
+            __syncthreads();      // every thread has read s_k before warp 0 writes it again
+            continue;
+        }
+        const unsigned e = s_epoch;
+        const int c = (int)s_chunk;
+        const FlowProblem& P = probs[k];
+        if (e == 0) flow_init(P, c, red);
+        else if (e & 1u) flow_product(P, (int)((e - 1u) >> 1), s_scalar, c, red, vstage);
+        else flow_update(P, (int)((e >> 1) - 1u), s_scalar, c, red);
+        __threadfence();          // this chunk's writes, visible before it counts as done
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned d = atomicAdd(&ctl[k].done, 1u);
+            s_last = d + 1u == flow_chunks(P, e);
+        }
+        __syncthreads();
+        if (s_last && threadIdx.x < 32) {
+            __threadfence();
+            flow_transition(P, ctl[k], g, e);
+        }
+        __syncthreads();
     }
 }
 
@@ -202,6 +543,7 @@ struct Job {
     mlb_ctx* ctx = nullptr;
     mlb_status status = MLB_OK;
     double* Zd = nullptr;     // device Z (caller order) and kd order
+    bool flow = false;        // solved by the persistent launch
 };
 
 mlb_status setup_one(Job& j, const mlb_opts& o, cudaStream_t st) {
@@ -212,7 +554,7 @@ mlb_status setup_one(Job& j, const mlb_opts& o, cudaStream_t st) {
     s = mlb_build_basis(j.ctx, P.points, P.n, P.d, P.w);
     if (s != MLB_OK) return s;
     // the persistent launch reads the row panels of the systems it solves
-    j.ctx->allow_sym = j.ctx->nwav > kCtaRows;
+    j.ctx->allow_sym = j.ctx->nwav > kFlowCols;
     s = mlb_assemble(j.ctx, &P.theta, P.tau_factor);
     if (s != MLB_OK) return s;
     mlb_ctx* c = j.ctx;
@@ -231,6 +573,7 @@ mlb_status finish_one(Job& j) {
     MLB_CUDA(c, cudaMemcpyAsync(&hs, c->pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, c->stream));
     MLB_CUDA(c, cudaStreamSynchronize(c->stream));
     P.iterations = hs.it;
+    if (j.flow && !hs.done) return fail(c, MLB_ETIMEOUT, "the persistent PCG stopped before this problem finished");
     mlb_status s = apply_Wt_dev(c, c->gW, c->gamma);
     if (s != MLB_OK) return s;
     s = trend_dev(c, c->vec + 6 * c->N);
@@ -315,57 +658,124 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
     for (auto& s : streams) cudaStreamSynchronize(s);
     g_batch_phase_ms[0] = ms_since(tp);
     tp = std::chrono::steady_clock::now();
-    // phase 2: the small systems in one persistent launch (largest first, so
-    // the longest CTAs start first), the large ones on the stream pool
+    // phase 2: every system of at most kFlowCols unknowns in one persistent
+    // launch (largest first), larger ones on the stream pool meanwhile
     std::vector<int> order, big;
     for (int i = 0; i < count; ++i)
-        if (jobs[i].status == MLB_OK) (jobs[i].ctx->nwav > kCtaRows ? big : order).push_back(i);
+        if (jobs[i].status == MLB_OK) (jobs[i].ctx->nwav > kFlowCols ? big : order).push_back(i);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].ctx->nwav > jobs[b].ctx->nwav; });
-    std::vector<BatchPcgProblem> hp;
+    std::vector<FlowProblem> hp;
+    std::vector<double> weight;
+    int64_t partTotal = 0;
+    int maxWidth = 4;
     for (int i : order) {
         mlb_ctx* c = jobs[i].ctx;
-        BatchPcgProblem b{};
-        b.vals64 = c->pan.vals32 ? nullptr : c->pan.vals;
-        b.vals32 = c->pan.vals32;
-        b.colidx = c->pan.colidx;
-        b.ncols = c->pan.ncols;
-        b.valOff = c->pan.valOff;
-        b.colOff = c->pan.colOff;
-        b.rowCell = c->pan.rowCell;
-        b.wOff = c->cells.wOff;
-        b.diag = o.precond ? c->diag : nullptr;
-        b.n = c->nwav;
-        b.b = c->vec;
-        b.x = c->gW;
-        b.r = c->vec + b.n;
-        b.z = c->vec + 2 * b.n;
-        b.p = c->vec + 3 * b.n;
-        b.q = c->vec + 4 * b.n;
-        b.tol2 = o.pcg_rtol * o.pcg_rtol;
-        b.maxit = o.pcg_maxit;
-        b.st = c->pcg;
-        hp.push_back(b);
+        jobs[i].flow = true;
+        FlowProblem f{};
+        f.vals32 = c->pan.vals32;
+        f.vals64 = c->pan.vals32 ? nullptr : c->pan.vals;
+        f.colidx = c->pan.colidx;
+        f.ncols = c->pan.ncols;
+        f.valOff = c->pan.valOff;
+        f.colOff = c->pan.colOff;
+        f.rowCell = c->pan.rowCell;
+        f.wOff = c->cells.wOff;
+        f.diag = o.precond ? c->diag : nullptr;
+        const int n = (int)c->nwav;
+        f.n = n;
+        f.width = (n + 3) & ~3;
+        f.dense = c->pan.nnz == (int64_t)n * n ? 1 : 0;
+        f.prodRows = f.dense ? kFlowDenseRows
+                             : (int)std::max<int64_t>(8, std::min<int64_t>(n, kProdValues / f.width));
+        f.nprod = (n + f.prodRows - 1) / f.prodRows;
+        f.nupd = (n + kUpdRows - 1) / kUpdRows;
+        f.b = c->vec;
+        f.x = c->gW;
+        f.r = c->vec + n;
+        f.z = c->vec + 2 * n;
+        f.p0 = c->vec + 3 * n;
+        f.q = c->vec + 4 * n;
+        f.p1 = c->vec + 5 * n;
+        f.tol2 = o.pcg_rtol * o.pcg_rtol;
+        f.maxit = o.pcg_maxit;
+        f.st = c->pcg;
+        partTotal += 2 * std::max(f.nprod, f.nupd);
+        maxWidth = std::max(maxWidth, f.width);
+        weight.push_back((double)c->pan.stored + 1.0);
+        hp.push_back(f);
     }
     mlb_status first = MLB_OK;
-    BatchPcgProblem* dp = nullptr;
+    FlowProblem* dp = nullptr;
+    FlowCtl* dctl = nullptr;
+    FlowGlobal* dg = nullptr;
+    double* dpart = nullptr;
+    int* dhome = nullptr;
     cudaStream_t ps = nullptr;
+    auto flow_err = [&](mlb_status st, const std::string& what) {
+        if (first == MLB_OK) {
+            first = st;
+            g_batch_err = what;
+        }
+    };
     if (!hp.empty()) {
-        if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaMalloc(&dp, sizeof(BatchPcgProblem) * hp.size()) != cudaSuccess) {
-            first = MLB_ENOMEM;
-            g_batch_err = "stream or problem table for the persistent PCG";
+        int dev = o.device, nsm = 0, perSm = 0, optin = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const size_t smem = sizeof(double) * (size_t)maxWidth;
+        cudaFuncAttributes fa{};
+        cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)batch_flow_pcg_kernel);
+        // the process-wide opt-in is always the device maximum, so concurrent
+        // calls on other host threads cannot lower it under each other
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute((const void*)batch_flow_pcg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSm, batch_flow_pcg_kernel, kFlowThreads, smem);
+        if (e != cudaSuccess || perSm < 1) {
+            cudaGetLastError();
+            flow_err(MLB_ECUDA, std::string("batch_flow_pcg_kernel setup: ") + cudaGetErrorString(e));
+        }
+        const int grid = std::max(1, nsm * std::max(perSm, 1));
+        // CTAs start spread over the problems in proportion to their panel sizes
+        std::vector<int> home(grid);
+        {
+            double total = 0.0;
+            for (double w : weight) total += w;
+            double acc = 0.0;
+            int k = 0;
+            for (int b = 0; b < grid; ++b) {
+                const double target = (b + 0.5) / grid * total;
+                while (k + 1 < (int)weight.size() && acc + weight[k] <= target) acc += weight[k++];
+                home[b] = k;
+            }
+        }
+        int64_t partOff = 0;
+        if (first == MLB_OK &&
+            (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaMalloc(&dp, sizeof(FlowProblem) * hp.size()) != cudaSuccess ||
+             cudaMalloc(&dctl, sizeof(FlowCtl) * hp.size()) != cudaSuccess ||
+             cudaMalloc(&dg, sizeof(FlowGlobal)) != cudaSuccess ||
+             cudaMalloc(&dpart, sizeof(double) * std::max<int64_t>(partTotal, 1)) != cudaSuccess ||
+             cudaMalloc(&dhome, sizeof(int) * grid) != cudaSuccess)) {
+            cudaGetLastError();
+            flow_err(MLB_ENOMEM, "stream or tables for the persistent PCG");
         }
         if (first == MLB_OK) {
-            cudaError_t e = cudaMemcpyAsync(dp, hp.data(), sizeof(BatchPcgProblem) * hp.size(),
-                                            cudaMemcpyHostToDevice, ps);
+            for (auto& f : hp) {
+                f.part = dpart + partOff;
+                partOff += 2 * std::max(f.nprod, f.nupd);
+            }
+            FlowGlobal hg{};
+            hg.remaining = (int)hp.size();
+            e = cudaMemcpyAsync(dp, hp.data(), sizeof(FlowProblem) * hp.size(), cudaMemcpyHostToDevice, ps);
+            if (e == cudaSuccess) e = cudaMemsetAsync(dctl, 0, sizeof(FlowCtl) * hp.size(), ps);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dg, &hg, sizeof(FlowGlobal), cudaMemcpyHostToDevice, ps);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dhome, home.data(), sizeof(int) * grid, cudaMemcpyHostToDevice, ps);
             if (e == cudaSuccess) {
-                batch_pcg_kernel<<<(unsigned)hp.size(), 512, 0, ps>>>(dp);
+                batch_flow_pcg_kernel<<<(unsigned)grid, kFlowThreads, smem, ps>>>(dp, dctl, (int)hp.size(), dhome, dg);
                 e = cudaGetLastError();
             }
-            if (e != cudaSuccess) {
-                first = MLB_ECUDA;
-                g_batch_err = std::string("batch_pcg_kernel: ") + cudaGetErrorString(e);
-            }
+            if (e != cudaSuccess) flow_err(MLB_ECUDA, std::string("batch_flow_pcg_kernel: ") + cudaGetErrorString(e));
         }
     }
     if (first == MLB_OK && !big.empty())
@@ -378,14 +788,16 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
             return (s == MLB_EBREAKDOWN || s == MLB_ENOCONV) ? MLB_OK : s;
         });
     if (ps) {
-        const cudaError_t e = cudaStreamSynchronize(ps);
-        if (e != cudaSuccess && first == MLB_OK) {
-            first = MLB_ECUDA;
-            g_batch_err = std::string("batch_pcg_kernel: ") + cudaGetErrorString(e);
-        }
+        FlowGlobal hg{};
+        cudaError_t e = cudaSuccess;
+        if (dg) e = cudaMemcpyAsync(&hg, dg, sizeof(FlowGlobal), cudaMemcpyDeviceToHost, ps);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
+        if (e != cudaSuccess) flow_err(MLB_ECUDA, std::string("batch_flow_pcg_kernel: ") + cudaGetErrorString(e));
+        else if (hg.err) flow_err(MLB_ETIMEOUT, "batch_flow_pcg_kernel: no problem made progress within the wait limit");
         cudaStreamDestroy(ps);
     }
-    if (dp) cudaFree(dp);
+    for (void* q : {(void*)dp, (void*)dctl, (void*)dg, (void*)dpart, (void*)dhome})
+        if (q) cudaFree(q);
     const int64_t persistent = (first == MLB_OK && !hp.empty()) ? 1 : 0;
     g_batch_phase_ms[1] = ms_since(tp);
     tp = std::chrono::steady_clock::now();

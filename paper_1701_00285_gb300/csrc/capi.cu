@@ -452,7 +452,17 @@ static mlb_status build_basis_host(mlb_ctx* ctx, const double* pts, int64_t N, i
     int hflag[4] = {0, 0, 0, 0};
     MLB_CUDA(ctx, cudaMemcpyAsync(hflag, ctx->flag, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
     MLB_CUDA(ctx, cudaStreamSynchronize(st));
-    if (hflag[0] & 1) return fail(ctx, MLB_ERANK, "a local moment matrix is rank deficient");
+    if (hflag[0] & 1) {
+        const int g = hflag[1] - 1;
+        std::string where;
+        if (g >= 0 && g < ncell) {
+            int l = 0;
+            while ((1 << (l + 1)) - 1 <= g) ++l;
+            where = " (cell " + std::to_string(g) + " of level " + std::to_string(l) + ": " +
+                    std::to_string(H[g].s) + " vectors, " + std::to_string(p) + " moments)";
+        }
+        return fail(ctx, MLB_ERANK, "a local moment matrix is rank deficient" + where);
+    }
     if (hflag[0] & 2) return fail(ctx, MLB_ERANK, "X^T X is not positive definite");
     ctx->state = 1;
     return MLB_OK;

@@ -24,7 +24,9 @@
 // commits them to an mbarrier, and eight warps read r^2 back with tcgen05.ld
 // (warp w: TMEM lanes 32 (w mod 4) .. +31, columns 128 (w div 4) .. +127),
 // evaluate phi and accumulate phi(r) a_j (FP32 sums per 32 columns, cascaded
-// with Sum2, FP64 across tiles).  Two CTAs per SM, each holding 256 TMEM
+// with Sum2, FP64 across tiles).  phi is evaluated in t = s log2(e): one
+// approximate square root of sc^2 r^2 and one 2^-t, both on the MUFU, and
+// the Matern polynomial in t on the FMA pipe.  Two CTAs per SM, each holding 256 TMEM
 // columns (the 512 of an SM); the dynamic shared memory requested keeps a
 // third CTA off the SM, so the allocation never waits.  Every wait is bounded.
 #include <cuda_bf16.h>
@@ -193,18 +195,49 @@ __device__ void write_corr(unsigned char* base, int row, float corr) {
     *reinterpret_cast<__nv_bfloat16*>(base + op_off<KG>(row, e + 2)) = l;
 }
 
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// phi at s = t ln 2, given t = s log2(e): e^-s = 2^-t (one MUFU operation),
+// the Matern polynomial rewritten in t
 template <int KIND>
-__device__ __forceinline__ float matern_fast(float r, float scale) {
-    const float s = scale * r;
-    const float e = __expf(-s);
+__device__ __forceinline__ float matern_t(float t) {
+    constexpr float kLn2 = 0.693147180559945309f;
+    const float e = ex2_approx(-t);
     if (KIND == 0) return e;
-    if (KIND == 1) return (1.0f + s) * e;
-    return fmaf(s, fmaf(s, 1.0f / 3.0f, 1.0f), 1.0f) * e;
+    if (KIND == 1) return fmaf(kLn2, t, 1.0f) * e;
+    return fmaf(t, fmaf(t, kLn2 * kLn2 / 3.0f, kLn2), 1.0f) * e;
+}
+
+// 32 accumulator columns of one target row: t = sqrt(sc2 r^2), phi, and the
+// weighted sums.  DIAG: the chunk may hold the row's own point (column
+// selfc), whose distance is set to zero exactly.
+template <int KIND, bool DIAG>
+__device__ __forceinline__ void tc_row_chunk(const float (&r2)[32], const float* __restrict__ wh,
+                                             const float* __restrict__ wl, float sc2, int selfc, float& ch,
+                                             float& suml) {
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        float q2 = fmaxf(r2[c], 0.0f) * sc2;
+        if (DIAG && c == selfc) q2 = 0.0f;
+        const float kv = matern_t<KIND>(sqrt_approx(q2));
+        ch = fmaf(kv, wh[c], ch);
+        suml = fmaf(kv, wl[c], suml);
+    }
 }
 
 template <int D, int KIND>
 __global__ void __launch_bounds__(kTcThreads, 2)
-    ksum_tc_kernel(const float* __restrict__ x32, const double* __restrict__ a, int64_t N, float scale,
+    ksum_tc_kernel(const float* __restrict__ x32, const double* __restrict__ a, int64_t N, float sc2,
                    int64_t jchunk, double* __restrict__ out, double* __restrict__ part, int* err) {
     using S = TcShape<D>;
     extern __shared__ __align__(1024) unsigned char sm_tc[];
@@ -306,23 +339,19 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         tc_fence_after();
         __syncthreads();
         if (bad) break;
-        // the self pairs: target i against source i of this tile
-        const bool selftile = my_i >= jt && my_i < jt + kTcN;
-        const int selfcol = (int)(my_i - jt);
+        // the self pairs: target i against source i of this tile; a chunk of
+        // 32 columns can hold them only where it meets the warp's 32 rows
+        const int64_t rowBase = i0 + quarter * 32;
 #pragma unroll 1
         for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
             float r2[32];
             tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, r2);
             float ch = 0.0f;
-#pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                float q2 = fmaxf(r2[c], 0.0f);
-                if (selftile && c0 + c == selfcol) q2 = 0.0f;
-                const float r = q2 * rsqrtf(fmaxf(q2, 1e-30f));
-                const float kv = matern_fast<KIND>(r, scale);
-                ch = fmaf(kv, wh[c0 + c], ch);
-                suml = fmaf(kv, wl[c0 + c], suml);
-            }
+            const int64_t colBase = jt + c0;
+            if (rowBase < colBase + 32 && colBase < rowBase + 32)
+                tc_row_chunk<KIND, true>(r2, wh + c0, wl + c0, sc2, (int)(my_i - colBase), ch, suml);
+            else
+                tc_row_chunk<KIND, false>(r2, wh + c0, wl + c0, sc2, 0, ch, suml);
             sum2_add(sumh, sume, ch);
         }
         acc += (double)sumh + ((double)sume + (double)suml);
@@ -375,13 +404,15 @@ bool launch_d(mlb_ctx* ctx, const double* a, double* out) {
         chunk = (chunk + kTcN - 1) / kTcN * kTcN;
         splits = (N + chunk - 1) / chunk;
     }
+    // t = s log2(e) = sc r: the epilogue's exponential is then one 2^-t
+    const double sc = ctx->kfn.scale * 1.4426950408889634;
     if (cudaFuncSetAttribute(ksum_tc_kernel<D, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) !=
         cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     ksum_tc_kernel<D, KIND><<<dim3((unsigned)ctasM, (unsigned)splits), kTcThreads, kTcSmem, ctx->stream>>>(
-        ctx->kxs32, a, N, ctx->kfn.scale32, chunk, out, splits > 1 ? ctx->ksum_part : nullptr, ctx->flag + 3);
+        ctx->kxs32, a, N, (float)(sc * sc), chunk, out, splits > 1 ? ctx->ksum_part : nullptr, ctx->flag + 3);
     ctx->launches += 1;
     if (splits > 1) {
         tc_reduce_kernel<<<(unsigned)std::min<int64_t>((N + 255) / 256, 4096), 256, 0, ctx->stream>>>(
