@@ -37,8 +37,8 @@ namespace mlb {
 constexpr int kFlowCols = 12288;
 constexpr int kFlowThreads = 256;
 constexpr int kFlowWarps = kFlowThreads / 32;
-constexpr int kUpdRows = 1024;                 // rows per chunk of the vector phases
-constexpr int kFlowDenseRows = 32;             // rows per product chunk, complete patterns (4 per warp)
+constexpr int kUpdRows = 512;                  // rows per chunk of the vector phases
+constexpr int kFlowDenseRows = 16;             // rows per product chunk, complete patterns (4 rows x 2 column halves per warp pair)
 constexpr int64_t kProdValues = 1 << 18;       // panel values per product chunk, truncated patterns
 constexpr int kFlowSpan = 2048;                // columns summed in FP32 before the FP64 sum
 
@@ -87,6 +87,7 @@ struct FlowCtl {
 };
 
 struct FlowGlobal {
+    unsigned long long hot;    // (iterations << 32 | problem) of the longest-running problem
     int remaining;             // problems not finished
     unsigned progress;         // epochs opened or problems finished, all problems
     int err;                   // set when no problem made progress for kWaitCycles
@@ -142,9 +143,11 @@ __device__ void flow_init(const FlowProblem& P, int c, double* red) {
 
 // Epoch 2i + 1, rows [r0, r1): p_i = z + beta p_(i-1) (p_0 as set up), staged
 // in shared memory (FP32 high and low parts for FP32 panels), q = C~_W p_i on
-// the chunk's rows, warp per row; partial p_i.q.  FP32 values are summed in
-// FP32 over each lane's 16 values of a 512-column step, the steps in FP64.
-__device__ void flow_product(const FlowProblem& P, int it, double beta, int c, double* red, double* vstage) {
+// the chunk's rows; partial p_i.q.  Complete patterns: 16 rows per chunk, see
+// below.  Truncated patterns: a warp per row through its column list, FP32
+// sums over each lane's 16 values of a 512-column step, the steps in FP64.
+__device__ void flow_product(const FlowProblem& P, int it, double beta, int c, double* red, double* vstage,
+                             bool staged, double* hsum, int64_t* rowoff) {
     const int r0 = c * P.prodRows, r1 = min(P.n, r0 + P.prodRows);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int w = P.width;
@@ -160,21 +163,41 @@ __device__ void flow_product(const FlowProblem& P, int it, double beta, int c, d
         const int g = P.rowCell[row];
         const int nc = P.ncols[g];
         const int64_t off = P.valOff[g] + (int64_t)(row - P.wOff[g]) * nc;
+        if (row - r0 < kFlowDenseRows) rowoff[row - r0] = off;    // kept for the dense product below
         const char* src = mixed ? (const char*)(P.vals32 + off) : (const char*)(P.vals64 + off);
         const unsigned bytes = (unsigned)nc * (mixed ? 4u : 8u);
         for (unsigned o = 0; o < bytes; o += 32768u)
             asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src + o), "r"(min(32768u, bytes - o))
                          : "memory");
     }
-    for (int j = threadIdx.x; j < w; j += kFlowThreads) {
-        double v = 0.0;
-        if (j < P.n) v = it == 0 ? __ldcg(P.p0 + j) : __ldcg(P.z + j) + beta * __ldcg(pold + j);
-        if (mixed) {
-            const float h = (float)v;
-            vh[j] = h;
-            vl[j] = (float)(v - (double)h);
-        } else {
-            vstage[j] = v;
+    // four columns per thread in flight: the staging is latency bound.  A
+    // CTA that already staged this problem's epoch keeps it.  Every chunk
+    // reads the same two vectors at about the same time, so each starts at
+    // its own block of columns: the requests spread over the L2 slices
+    // instead of queueing on the same lines.
+    const int nblk = (w + 4 * kFlowThreads - 1) / (4 * kFlowThreads);
+    for (int bi = staged ? nblk : 0; bi < nblk; ++bi) {
+        const int j0 = ((bi + c) % nblk) * 4 * kFlowThreads + threadIdx.x;
+        double zz[4], pp[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u * kFlowThreads;
+            const bool live = j < P.n;
+            zz[u] = live ? __ldcg((it == 0 ? P.p0 : P.z) + j) : 0.0;
+            pp[u] = (live && it > 0) ? __ldcg(pold + j) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u * kFlowThreads;
+            if (j >= w) break;
+            const double v = it == 0 ? zz[u] : zz[u] + beta * pp[u];
+            if (mixed) {
+                const float h = (float)v;
+                vh[j] = h;
+                vl[j] = (float)(v - (double)h);
+            } else {
+                vstage[j] = v;
+            }
         }
     }
     if (it > 0)
@@ -183,21 +206,26 @@ __device__ void flow_product(const FlowProblem& P, int it, double beta, int c, d
     __syncthreads();
     double pq = 0.0;
     if (P.dense) {
-        // every row holds all w columns in order: four rows per warp share
-        // each staged column load; FP32 sums over blocks of kFlowSpan
-        // columns, FP64 across blocks
-        for (int rg = r0 + 4 * warp; rg < r1; rg += 4 * kFlowWarps) {
-            const void* rowp[4];
+        // every row holds all w columns in order.  Warps 0-3 and 4-7 take the
+        // two column halves of the chunk's 16 rows, four rows per warp sharing
+        // each staged column load, so a chunk is half as many dependent load
+        // steps long; FP32 sums over blocks of kFlowSpan columns, FP64 across
+        // blocks and halves (half 0 + half 1, in that order)
+        const int step = mixed ? 256 : 128;
+        const int mid = min(w, (w / 2 + step - 1) / step * step);
+        const int half = warp >> 2;
+        const int cb = half ? mid : 0, ce = half ? w : mid;
+        const int rg = r0 + 4 * (warp & 3);
+        const void* rowp[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int row = min(rg + q, r1 - 1);
-                const int g = P.rowCell[row];
-                const int64_t off = P.valOff[g] + (int64_t)(row - P.wOff[g]) * w;
-                rowp[q] = mixed ? (const void*)(P.vals32 + off) : (const void*)(P.vals64 + off);
-            }
-            double acc[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int jb = 0; jb < w; jb += kFlowSpan) {
-                const int je = min(w, jb + kFlowSpan);
+        for (int q = 0; q < 4; ++q) {
+            const int64_t off = rowoff[min(rg + q, r1 - 1) - r0];
+            rowp[q] = mixed ? (const void*)(P.vals32 + off) : (const void*)(P.vals64 + off);
+        }
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        if (rg < r1) {
+            for (int jb = cb; jb < ce; jb += kFlowSpan) {
+                const int je = min(ce, jb + kFlowSpan);
                 if (mixed) {
                     float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
                     for (int j0 = jb + 4 * lane; j0 < je; j0 += 256) {
@@ -245,12 +273,20 @@ __device__ void flow_product(const FlowProblem& P, int it, double beta, int c, d
                     }
                 }
             }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        if (half == 1 && lane == 0)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) hsum[4 * (warp & 3) + q] = acc[q];
+        __syncthreads();
+        if (half == 0 && lane == 0) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                double a = acc[q];
-                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
                 const int row = rg + q;
-                if (lane == 0 && row < r1) {
+                if (row < r1) {
+                    const double a = acc[q] + hsum[4 * (warp & 3) + q];
                     P.q[row] = a;
                     const double prow = it == 0 ? __ldcg(P.p0 + row) : __ldcg(P.z + row) + beta * __ldcg(pold + row);
                     pq += prow * a;
@@ -338,12 +374,21 @@ __device__ void flow_update(const FlowProblem& P, int it, double alpha, int c, d
 __device__ __forceinline__ double2 flow_gather(const double* part, int nchunk, bool pairs) {
     const int lane = threadIdx.x & 31;
     double a = 0.0, b = 0.0;
-    for (int c = lane; c < nchunk; c += 32) {
-        if (pairs) {
-            a += __ldcg(part + 2 * c);
-            b += __ldcg(part + 2 * c + 1);
-        } else {
-            a += __ldcg(part + c);
+    // four slots per lane loaded before any is added (the sum order stays
+    // lane, lane + 32, lane + 64, ...)
+    for (int c0 = lane; c0 < nchunk; c0 += 128) {
+        double va[4], vb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = c0 + 32 * u;
+            va[u] = c < nchunk ? __ldcg(part + (pairs ? 2 * c : c)) : 0.0;
+            vb[u] = (pairs && c < nchunk) ? __ldcg(part + 2 * c + 1) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (c0 + 32 * u >= nchunk) break;
+            a += va[u];
+            b += vb[u];
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -375,7 +420,7 @@ __device__ void flow_finish(const FlowProblem& P, FlowCtl& C, FlowGlobal* g, int
 // The last finisher of epoch e: reduce, test, set the scalars, open e + 1.
 // Run by warp 0; lane 0 writes.  Matches pcg_run: x0 = 0, stop when
 // ||r_k||^2 <= tol^2 ||b||^2 on the recursive unpreconditioned residual.
-__device__ void flow_transition(const FlowProblem& P, FlowCtl& C, FlowGlobal* g, unsigned e) {
+__device__ void flow_transition(const FlowProblem& P, FlowCtl& C, FlowGlobal* g, unsigned e, int k) {
     const int lane = threadIdx.x & 31;
     if (e == 0) {
         const double2 s = flow_gather(P.part, P.nupd, true);
@@ -412,6 +457,9 @@ __device__ void flow_transition(const FlowProblem& P, FlowCtl& C, FlowGlobal* g,
             } else {
                 C.beta = s.y / C.rz;
                 C.rz = s.y;
+                // the problem with most iterations so far is offered first:
+                // a long solve is the batch's critical path
+                atomicMax(&g->hot, ((unsigned long long)it << 32) | (unsigned)k);
                 flow_open(C, g, e + 1u);
             }
         }
@@ -429,10 +477,18 @@ __global__ void __launch_bounds__(kFlowThreads, 3) batch_flow_pcg_kernel(const F
     extern __shared__ __align__(16) double vstage[];
     __shared__ double red[2 * kFlowWarps];
     __shared__ int s_k, s_exit, s_last;
+    __shared__ int s_stk;                  // problem and epoch whose direction is staged
+    __shared__ unsigned s_ste;
+    __shared__ double hsum[kFlowDenseRows];
+    __shared__ int64_t rowoff[kFlowDenseRows];   // panel offsets of a dense chunk's rows
     __shared__ unsigned s_chunk, s_epoch;
     __shared__ double s_scalar;
     const int lane = threadIdx.x & 31;
     int cur = home[blockIdx.x];
+    if (threadIdx.x == 0) {
+        s_stk = -1;
+        s_ste = 0;
+    }
     bool idle = false;
     unsigned seen = 0;
     long long idle0 = 0;
@@ -440,15 +496,33 @@ __global__ void __launch_bounds__(kFlowThreads, 3) batch_flow_pcg_kernel(const F
         if (threadIdx.x < 32) {
             int k = -1;
             unsigned chunk = 0, epoch = 0;
+            {
+                // the longest-running problem first
+                int hk = -1;
+                if (lane == 0) {
+                    const unsigned long long h = *(volatile unsigned long long*)&g->hot;
+                    const int kh = (int)(unsigned)(h & 0xffffffffull);
+                    if (kh < count) {
+                        const unsigned long long t = *(volatile unsigned long long*)&ctl[kh].ticket;
+                        if ((unsigned)t < flow_chunks(probs[kh], (unsigned)(t >> 32))) {
+                            const unsigned long long t2 = atomicAdd(&ctl[kh].ticket, 1ull);
+                            epoch = (unsigned)(t2 >> 32);
+                            chunk = (unsigned)t2;
+                            if (chunk < flow_chunks(probs[kh], epoch)) hk = kh;
+                        }
+                    }
+                }
+                k = __shfl_sync(0xffffffffu, hk, 0);
+            }
             for (int base = 0; base < count && k < 0; base += 32) {
                 const int j = base + lane;
                 bool cand = false;
                 if (j < count) {
+                    // a finished problem shows no open chunk: its last epoch's
+                    // chunks were all handed out
                     const int kk = (cur + j) % count;
-                    if (!*(volatile int*)&ctl[kk].finished) {
-                        const unsigned long long t = *(volatile unsigned long long*)&ctl[kk].ticket;
-                        cand = (unsigned)t < flow_chunks(probs[kk], (unsigned)(t >> 32));
-                    }
+                    const unsigned long long t = *(volatile unsigned long long*)&ctl[kk].ticket;
+                    cand = (unsigned)t < flow_chunks(probs[kk], (unsigned)(t >> 32));
                 }
                 unsigned m = __ballot_sync(0xffffffffu, cand);
                 while (m && k < 0) {
@@ -507,7 +581,14 @@ __global__ void __launch_bounds__(kFlowThreads, 3) batch_flow_pcg_kernel(const F
         const int c = (int)s_chunk;
         const FlowProblem& P = probs[k];
         if (e == 0) flow_init(P, c, red);
-        else if (e & 1u) flow_product(P, (int)((e - 1u) >> 1), s_scalar, c, red, vstage);
+        else if (e & 1u) {
+            const bool staged = s_stk == k && s_ste == e;
+            flow_product(P, (int)((e - 1u) >> 1), s_scalar, c, red, vstage, staged, hsum, rowoff);
+            if (threadIdx.x == 0) {
+                s_stk = k;
+                s_ste = e;
+            }
+        }
         else flow_update(P, (int)((e >> 1) - 1u), s_scalar, c, red);
         __threadfence();          // this chunk's writes, visible before it counts as done
         __syncthreads();
@@ -518,7 +599,7 @@ __global__ void __launch_bounds__(kFlowThreads, 3) batch_flow_pcg_kernel(const F
         __syncthreads();
         if (s_last && threadIdx.x < 32) {
             __threadfence();
-            flow_transition(P, ctl[k], g, e);
+            flow_transition(P, ctl[k], g, e, k);
         }
         __syncthreads();
     }
