@@ -466,6 +466,25 @@ __device__ void flow_transition(const FlowProblem& P, FlowCtl& C, FlowGlobal* g,
     }
 }
 
+// Lane 0 of a searching warp: takes chunks of problem P's open epoch, if it
+// has any.  A grab is about one CTA's share when the live problems split the
+// grid evenly: whole epochs while hundreds of problems run (the direction is
+// then staged once per CTA and epoch), single chunks once one problem is
+// left, so that it spreads over the whole GPU.  Returns the number taken.
+__device__ __forceinline__ unsigned flow_take(const FlowProblem& P, FlowCtl& C, unsigned live, unsigned& epoch,
+                                              unsigned& chunk) {
+    const unsigned long long t = *(volatile unsigned long long*)&C.ticket;
+    const unsigned n0 = flow_chunks(P, (unsigned)(t >> 32));
+    if ((unsigned)t >= n0) return 0;
+    const unsigned long long share = (unsigned long long)n0 * live / gridDim.x;
+    const unsigned m = (unsigned)min((unsigned long long)n0, max(1ull, share));
+    const unsigned long long t2 = atomicAdd(&C.ticket, (unsigned long long)m);
+    epoch = (unsigned)(t2 >> 32);
+    chunk = (unsigned)t2;
+    const unsigned n = flow_chunks(P, epoch);
+    return chunk < n ? min(m, n - chunk) : 0u;
+}
+
 // All problems' PCGs in one launch.  Each CTA starts at its home problem
 // (CTAs spread over the problems in proportion to their panel sizes), takes
 // chunks of whatever epoch is open there, and moves on to other problems
@@ -481,7 +500,7 @@ __global__ void __launch_bounds__(kFlowThreads, 3) batch_flow_pcg_kernel(const F
     __shared__ unsigned s_ste;
     __shared__ double hsum[kFlowDenseRows];
     __shared__ int64_t rowoff[kFlowDenseRows];   // panel offsets of a dense chunk's rows
-    __shared__ unsigned s_chunk, s_epoch;
+    __shared__ unsigned s_chunk, s_count, s_epoch;
     __shared__ double s_scalar;
     const int lane = threadIdx.x & 31;
     int cur = home[blockIdx.x];
@@ -495,7 +514,8 @@ __global__ void __launch_bounds__(kFlowThreads, 3) batch_flow_pcg_kernel(const F
     while (true) {
         if (threadIdx.x < 32) {
             int k = -1;
-            unsigned chunk = 0, epoch = 0;
+            unsigned chunk = 0, epoch = 0, taken = 0;
+            const unsigned live = (unsigned)max(1, *(volatile int*)&g->remaining);
             {
                 // the longest-running problem first
                 int hk = -1;
@@ -503,13 +523,8 @@ __global__ void __launch_bounds__(kFlowThreads, 3) batch_flow_pcg_kernel(const F
                     const unsigned long long h = *(volatile unsigned long long*)&g->hot;
                     const int kh = (int)(unsigned)(h & 0xffffffffull);
                     if (kh < count) {
-                        const unsigned long long t = *(volatile unsigned long long*)&ctl[kh].ticket;
-                        if ((unsigned)t < flow_chunks(probs[kh], (unsigned)(t >> 32))) {
-                            const unsigned long long t2 = atomicAdd(&ctl[kh].ticket, 1ull);
-                            epoch = (unsigned)(t2 >> 32);
-                            chunk = (unsigned)t2;
-                            if (chunk < flow_chunks(probs[kh], epoch)) hk = kh;
-                        }
+                        taken = flow_take(probs[kh], ctl[kh], live, epoch, chunk);
+                        if (taken) hk = kh;
                     }
                 }
                 k = __shfl_sync(0xffffffffu, hk, 0);
@@ -531,10 +546,8 @@ __global__ void __launch_bounds__(kFlowThreads, 3) batch_flow_pcg_kernel(const F
                     const int kk = (cur + base + l) % count;
                     int got = 0;
                     if (lane == 0) {
-                        const unsigned long long t = atomicAdd(&ctl[kk].ticket, 1ull);
-                        epoch = (unsigned)(t >> 32);
-                        chunk = (unsigned)t;
-                        got = chunk < flow_chunks(probs[kk], epoch);
+                        taken = flow_take(probs[kk], ctl[kk], live, epoch, chunk);
+                        got = taken > 0;
                     }
                     if (__shfl_sync(0xffffffffu, got, 0)) k = kk;
                 }
@@ -561,6 +574,7 @@ __global__ void __launch_bounds__(kFlowThreads, 3) batch_flow_pcg_kernel(const F
                 }
                 s_k = k;
                 s_chunk = chunk;
+                s_count = taken;
                 s_epoch = epoch;
                 s_exit = ex;
                 if (k >= 0) {
@@ -578,23 +592,26 @@ __global__ void __launch_bounds__(kFlowThreads, 3) batch_flow_pcg_kernel(const F
             continue;
         }
         const unsigned e = s_epoch;
-        const int c = (int)s_chunk;
+        const unsigned c0 = s_chunk, cnt = s_count;
         const FlowProblem& P = probs[k];
-        if (e == 0) flow_init(P, c, red);
-        else if (e & 1u) {
-            const bool staged = s_stk == k && s_ste == e;
-            flow_product(P, (int)((e - 1u) >> 1), s_scalar, c, red, vstage, staged, hsum, rowoff);
-            if (threadIdx.x == 0) {
-                s_stk = k;
-                s_ste = e;
+        for (unsigned c = c0; c < c0 + cnt; ++c) {
+            if (e == 0) flow_init(P, (int)c, red);
+            else if (e & 1u) {
+                const bool staged = s_stk == k && s_ste == e;
+                flow_product(P, (int)((e - 1u) >> 1), s_scalar, (int)c, red, vstage, staged, hsum, rowoff);
+                if (threadIdx.x == 0) {
+                    s_stk = k;
+                    s_ste = e;
+                }
             }
+            else flow_update(P, (int)((e >> 1) - 1u), s_scalar, (int)c, red);
+            __syncthreads();      // s_stk, s_ste and the reduction scratch, before the next chunk
         }
-        else flow_update(P, (int)((e >> 1) - 1u), s_scalar, c, red);
-        __threadfence();          // this chunk's writes, visible before it counts as done
+        __threadfence();          // these chunks' writes, visible before they count as done
         __syncthreads();
         if (threadIdx.x == 0) {
-            const unsigned d = atomicAdd(&ctl[k].done, 1u);
-            s_last = d + 1u == flow_chunks(P, e);
+            const unsigned d = atomicAdd(&ctl[k].done, cnt);
+            s_last = d + cnt == flow_chunks(P, e);
         }
         __syncthreads();
         if (s_last && threadIdx.x < 32) {
