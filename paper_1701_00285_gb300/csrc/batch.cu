@@ -40,6 +40,10 @@ constexpr int kFlowWarps = kFlowThreads / 32;
 constexpr int kUpdRows = 512;                  // rows per chunk of the vector phases
 constexpr int kFlowDenseRows = 16;             // rows per product chunk, complete patterns (4 rows x 2 column halves per warp pair)
 constexpr int64_t kProdValues = 1 << 18;       // panel values per product chunk, truncated patterns
+constexpr int kFlowSymSeg = 512;               // columns per product chunk, symmetric storage (8 tiles)
+// shared scratch of a symmetric chunk, in doubles: p on the rows and columns
+// in FP64 and in FP32 high and low parts, and eight warps' column sums
+constexpr int kFlowSymSmem = (kSymRows + kFlowSymSeg) + (kSymRows + kFlowSymSeg) + 8 * 256 / 2;
 constexpr int kFlowSpan = 2048;                // columns summed in FP32 before the FP64 sum
 
 // One problem of the persistent launch: its panels (row panels of C~_W, FP32
@@ -62,6 +66,13 @@ struct FlowProblem {
     double* p1;                // and of odd ones
     double* q;
     double* part;              // per chunk of the current phase: its partial sums
+    // symmetric FP32 storage (mixed precision, complete pattern): the chunks
+    // of a product are (row block, column segment) pairs
+    const float* symVals;      // nullptr: row panels
+    const int64_t* symOff;     // per row block: offset of its first value
+    const int2* symItem;       // per chunk: (block, segment)
+    float* rowpart;            // nsegSym x n: a segment's sums over the block's rows
+    float* colpart;            // nblk x n: a block's sums over the columns right of its square
     PcgState* st;
     double tol2;
     int n;
@@ -348,6 +359,142 @@ __device__ void flow_product(const FlowProblem& P, int it, double beta, int c, d
     if (threadIdx.x == 0) P.part[c] = s.x;
 }
 
+// Epoch 2i + 1 on the symmetric FP32 storage: chunk c is block b's 128 rows
+// against its column segment s (kFlowSymSeg columns of its stored width,
+// which starts at its own diagonal square).  Every stored value is read once
+// and used twice: A[r][j] p_j goes to row r (FP32 over the segment, into
+// rowpart[s][r]) and, for columns j right of the diagonal square, A[r][j] p_r
+// to column j (FP32 over the block's rows, into colpart[b][j]); the update
+// epoch adds the pieces of each q_r in a fixed order.  Only the block's rows
+// and the segment's columns of p_i = z + beta p_(i-1) are staged (FP32 high
+// and low parts, and FP64 for the partial p_i.q).  Warp w takes rows w, w +
+// 8, ..., four at a time; a lane takes columns 4 lane and 128 + 4 lane of
+// each 256-column step (tiles lane / 16 and 2 + lane / 16).
+__device__ void flow_product_sym(const FlowProblem& P, int it, double beta, int c, double* red, double* smd) {
+    const int2 item = P.symItem[c];
+    const int b = item.x, sg = item.y;
+    const int n = P.n;
+    const int row0 = b * kSymRows, rows = min(kSymRows, n - row0);
+    const int W = (int)sym_width(n, b);
+    const int cs = row0 + sg * kFlowSymSeg, ce = min(row0 + W, cs + kFlowSymSeg);   // columns, multiples of 64
+    const int diagEnd = row0 + kSymRows;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double* pnew = flow_dir(P, it);
+    const double* pold = flow_dir(P, it + 1);
+    // shared scratch: row and column parts of p (FP64, FP32 high, FP32 low),
+    // then the eight warps' column sums of one step
+    double* vrd = smd;                                   // kSymRows
+    double* vcd = vrd + kSymRows;                        // kFlowSymSeg
+    float* vrh = reinterpret_cast<float*>(vcd + kFlowSymSeg);
+    float* vrl = vrh + kSymRows;
+    float* vch = vrl + kSymRows;
+    float* vcl = vch + kFlowSymSeg;
+    float* cred = vcl + kFlowSymSeg;                     // 8 x 256
+    const float* vb = P.symVals + P.symOff[b];
+    const int64_t tstride = (int64_t)rows * kSymTile;     // values per tile
+    // the segment's tiles towards L2 (each tile one contiguous block)
+    if (threadIdx.x < (ce - cs) / kSymTile)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(vb + ((cs - row0) / kSymTile + threadIdx.x) * tstride),
+                     "r"((unsigned)(tstride * 4))
+                     : "memory");
+    for (int t = threadIdx.x; t < kSymRows + kFlowSymSeg; t += kFlowThreads) {
+        const int j = t < kSymRows ? row0 + t : cs + (t - kSymRows);
+        const bool live = t < kSymRows ? t < rows : (j < ce && j < n);
+        double v = 0.0;
+        if (live) v = it == 0 ? __ldcg(P.p0 + j) : __ldcg(P.z + j) + beta * __ldcg(pold + j);
+        const float h = (float)v, l = (float)(v - (double)h);
+        if (t < kSymRows) {
+            vrd[t] = v;
+            vrh[t] = h;
+            vrl[t] = l;
+            if (it > 0 && sg == 0 && live) pnew[j] = v;     // each row's block has one segment 0
+        } else {
+            vcd[t - kSymRows] = v;
+            vch[t - kSymRows] = h;
+            vcl[t - kSymRows] = l;
+        }
+    }
+    __syncthreads();
+    constexpr int RW = kSymRows / kFlowWarps;   // rows per warp (16)
+    float racc[RW];
+#pragma unroll
+    for (int k = 0; k < RW; ++k) racc[k] = 0.0f;
+    double pq = 0.0;
+    const int j0 = 4 * lane, j1 = 128 + 4 * lane;
+    for (int c0 = cs; c0 < ce; c0 += 256) {
+        const int m = min(256, ce - c0);            // a multiple of 64
+        const bool ok0 = j0 < m, ok1 = j1 < m;
+        const int cb = c0 - cs;                     // first column of the step within the segment
+        const float4 h0 = ok0 ? *reinterpret_cast<const float4*>(vch + cb + j0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 l0 = ok0 ? *reinterpret_cast<const float4*>(vcl + cb + j0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 h1 = ok1 ? *reinterpret_cast<const float4*>(vch + cb + j1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 l1 = ok1 ? *reinterpret_cast<const float4*>(vcl + cb + j1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float* vc0 = vb + ((c0 - row0) / kSymTile + (lane >> 4)) * tstride + 4 * (lane & 15);
+        const float* vc1 = vc0 + 2 * tstride;
+        float ca[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) ca[k] = 0.0f;
+#pragma unroll
+        for (int k0 = 0; k0 < RW; k0 += 4) {
+            float4 a[4][2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = min(warp + kFlowWarps * (k0 + q), rows - 1);
+                a[q][0] = ok0 ? __ldg(reinterpret_cast<const float4*>(vc0 + r * kSymTile)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                a[q][1] = ok1 ? __ldg(reinterpret_cast<const float4*>(vc1 + r * kSymTile)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = warp + kFlowWarps * (k0 + q);
+                const float4 x = a[q][0], y = a[q][1];
+                float t = 0.0f;
+                t = fmaf(x.x, h0.x, t); t = fmaf(x.y, h0.y, t); t = fmaf(x.z, h0.z, t); t = fmaf(x.w, h0.w, t);
+                t = fmaf(y.x, h1.x, t); t = fmaf(y.y, h1.y, t); t = fmaf(y.z, h1.z, t); t = fmaf(y.w, h1.w, t);
+                t = fmaf(x.x, l0.x, t); t = fmaf(x.y, l0.y, t); t = fmaf(x.z, l0.z, t); t = fmaf(x.w, l0.w, t);
+                t = fmaf(y.x, l1.x, t); t = fmaf(y.y, l1.y, t); t = fmaf(y.z, l1.z, t); t = fmaf(y.w, l1.w, t);
+                racc[k0 + q] += t;
+                const float wh = vrh[r], wl = vrl[r];    // zero past the block's last row
+                ca[0] = fmaf(x.x, wh, fmaf(x.x, wl, ca[0]));
+                ca[1] = fmaf(x.y, wh, fmaf(x.y, wl, ca[1]));
+                ca[2] = fmaf(x.z, wh, fmaf(x.z, wl, ca[2]));
+                ca[3] = fmaf(x.w, wh, fmaf(x.w, wl, ca[3]));
+                ca[4] = fmaf(y.x, wh, fmaf(y.x, wl, ca[4]));
+                ca[5] = fmaf(y.y, wh, fmaf(y.y, wl, ca[5]));
+                ca[6] = fmaf(y.z, wh, fmaf(y.z, wl, ca[6]));
+                ca[7] = fmaf(y.w, wh, fmaf(y.w, wl, ca[7]));
+            }
+        }
+        *reinterpret_cast<float4*>(cred + warp * 256 + j0) = make_float4(ca[0], ca[1], ca[2], ca[3]);
+        *reinterpret_cast<float4*>(cred + warp * 256 + j1) = make_float4(ca[4], ca[5], ca[6], ca[7]);
+        __syncthreads();
+        // one thread per column right of the diagonal square: the eight warps' sums in order
+        {
+            const int t = threadIdx.x;
+            const int col = c0 + t;
+            if (t < m && col >= diagEnd && col < n) {
+                float sum = 0.0f;
+#pragma unroll
+                for (int w8 = 0; w8 < kFlowWarps; ++w8) sum += cred[w8 * 256 + t];
+                P.colpart[(int64_t)b * n + col] = sum;
+                pq += vcd[cb + t] * (double)sum;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < RW; ++k) {
+        float a = racc[k];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        const int r = warp + kFlowWarps * k;
+        if (lane == 0 && r < rows) {
+            P.rowpart[(int64_t)sg * n + row0 + r] = a;
+            pq += vrd[r] * (double)a;
+        }
+    }
+    const double2 s2 = flow_sum2(pq, 0.0, red);
+    if (threadIdx.x == 0) P.part[c] = s2.x;
+}
+
 // Epoch 2i + 2, rows [r0, r1): x += alpha p_i, r -= alpha q, z = D^-1 r;
 // partials r.r and r.z.
 __device__ void flow_update(const FlowProblem& P, int it, double alpha, int c, double* red) {
@@ -356,7 +503,19 @@ __device__ void flow_update(const FlowProblem& P, int it, double alpha, int c, d
     double rr = 0.0, rz = 0.0;
     for (int i = r0 + threadIdx.x; i < r1; i += kFlowThreads) {
         P.x[i] = __ldcg(P.x + i) + alpha * __ldcg(p + i);
-        const double ri = __ldcg(P.r + i) - alpha * __ldcg(P.q + i);
+        double qi;
+        if (P.symVals) {
+            // q_i: the row sums of its block's segments, then the column sums
+            // of the blocks above it, in that order
+            const int bi = i / kSymRows;
+            const int ns = (int)((sym_width(P.n, bi) + kFlowSymSeg - 1) / kFlowSymSeg);
+            qi = 0.0;
+            for (int sgi = 0; sgi < ns; ++sgi) qi += (double)__ldcg(P.rowpart + (int64_t)sgi * P.n + i);
+            for (int bb = 0; bb < bi; ++bb) qi += (double)__ldcg(P.colpart + (int64_t)bb * P.n + i);
+        } else {
+            qi = __ldcg(P.q + i);
+        }
+        const double ri = __ldcg(P.r + i) - alpha * qi;
         P.r[i] = ri;
         const double zi = P.diag ? ri / P.diag[i] : ri;
         P.z[i] = zi;
@@ -596,6 +755,9 @@ __global__ void __launch_bounds__(kFlowThreads, 3) batch_flow_pcg_kernel(const F
         const FlowProblem& P = probs[k];
         for (unsigned c = c0; c < c0 + cnt; ++c) {
             if (e == 0) flow_init(P, (int)c, red);
+            else if ((e & 1u) && P.symVals) {
+                flow_product_sym(P, (int)((e - 1u) >> 1), s_scalar, (int)c, red, vstage);
+            }
             else if (e & 1u) {
                 const bool staged = s_stk == k && s_ste == e;
                 flow_product(P, (int)((e - 1u) >> 1), s_scalar, (int)c, red, vstage, staged, hsum, rowoff);
@@ -652,7 +814,9 @@ mlb_status setup_one(Job& j, const mlb_opts& o, cudaStream_t st) {
     s = mlb_build_basis(j.ctx, P.points, P.n, P.d, P.w);
     if (s != MLB_OK) return s;
     // the persistent launch reads the row panels of the systems it solves
-    j.ctx->allow_sym = j.ctx->nwav > kFlowCols;
+    // complete patterns of the mixed path get the symmetric FP32 storage
+    // (both the persistent launch and the single-problem PCG use it)
+    j.ctx->allow_sym = true;
     s = mlb_assemble(j.ctx, &P.theta, P.tau_factor);
     if (s != MLB_OK) return s;
     mlb_ctx* c = j.ctx;
@@ -764,7 +928,9 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].ctx->nwav > jobs[b].ctx->nwav; });
     std::vector<FlowProblem> hp;
     std::vector<double> weight;
-    int64_t partTotal = 0;
+    int64_t partTotal = 0, rowpartTotal = 0, colpartTotal = 0;
+    std::vector<int2> symItems;
+    std::vector<int64_t> symItemOff, rowpartOff, colpartOff;
     int maxWidth = 4;
     for (int i : order) {
         mlb_ctx* c = jobs[i].ctx;
@@ -797,9 +963,30 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
         f.tol2 = o.pcg_rtol * o.pcg_rtol;
         f.maxit = o.pcg_maxit;
         f.st = c->pcg;
+        if (c->sym.vals) {
+            // symmetric storage: (block, segment) chunks, block by block
+            f.symVals = c->sym.vals;
+            f.symOff = c->sym.off;
+            const int nblk = c->sym.nblk;
+            symItemOff.push_back((int64_t)symItems.size());
+            for (int bk = 0; bk < nblk; ++bk) {
+                const int ns = (int)((sym_width(n, bk) + kFlowSymSeg - 1) / kFlowSymSeg);
+                for (int sg = 0; sg < ns; ++sg) symItems.push_back(make_int2(bk, sg));
+            }
+            f.nprod = (int)(symItems.size() - symItemOff.back());
+            rowpartOff.push_back(rowpartTotal);
+            rowpartTotal += (int64_t)((sym_width(n, 0) + kFlowSymSeg - 1) / kFlowSymSeg) * n;
+            colpartOff.push_back(colpartTotal);
+            colpartTotal += (int64_t)nblk * n;
+            maxWidth = std::max(maxWidth, kFlowSymSmem);
+        } else {
+            symItemOff.push_back(-1);
+            rowpartOff.push_back(-1);
+            colpartOff.push_back(-1);
+        }
         partTotal += 2 * std::max(f.nprod, f.nupd);
         maxWidth = std::max(maxWidth, f.width);
-        weight.push_back((double)c->pan.stored + 1.0);
+        weight.push_back((double)(c->sym.vals ? c->sym.stored : c->pan.stored) + 1.0);
         hp.push_back(f);
     }
     mlb_status first = MLB_OK;
@@ -807,6 +994,9 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
     FlowCtl* dctl = nullptr;
     FlowGlobal* dg = nullptr;
     double* dpart = nullptr;
+    int2* dsymItem = nullptr;
+    float* drowpart = nullptr;
+    float* dcolpart = nullptr;
     int* dhome = nullptr;
     cudaStream_t ps = nullptr;
     auto flow_err = [&](mlb_status st, const std::string& what) {
@@ -854,18 +1044,29 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
              cudaMalloc(&dctl, sizeof(FlowCtl) * hp.size()) != cudaSuccess ||
              cudaMalloc(&dg, sizeof(FlowGlobal)) != cudaSuccess ||
              cudaMalloc(&dpart, sizeof(double) * std::max<int64_t>(partTotal, 1)) != cudaSuccess ||
+             cudaMalloc(&dsymItem, sizeof(int2) * std::max<size_t>(symItems.size(), 1)) != cudaSuccess ||
+             cudaMalloc(&drowpart, sizeof(float) * std::max<int64_t>(rowpartTotal, 1)) != cudaSuccess ||
+             cudaMalloc(&dcolpart, sizeof(float) * std::max<int64_t>(colpartTotal, 1)) != cudaSuccess ||
              cudaMalloc(&dhome, sizeof(int) * grid) != cudaSuccess)) {
             cudaGetLastError();
             flow_err(MLB_ENOMEM, "stream or tables for the persistent PCG");
         }
         if (first == MLB_OK) {
-            for (auto& f : hp) {
+            for (size_t q = 0; q < hp.size(); ++q) {
+                FlowProblem& f = hp[q];
                 f.part = dpart + partOff;
                 partOff += 2 * std::max(f.nprod, f.nupd);
+                if (f.symVals) {
+                    f.symItem = dsymItem + symItemOff[q];
+                    f.rowpart = drowpart + rowpartOff[q];
+                    f.colpart = dcolpart + colpartOff[q];
+                }
             }
             FlowGlobal hg{};
             hg.remaining = (int)hp.size();
             e = cudaMemcpyAsync(dp, hp.data(), sizeof(FlowProblem) * hp.size(), cudaMemcpyHostToDevice, ps);
+            if (e == cudaSuccess && !symItems.empty())
+                e = cudaMemcpyAsync(dsymItem, symItems.data(), sizeof(int2) * symItems.size(), cudaMemcpyHostToDevice, ps);
             if (e == cudaSuccess) e = cudaMemsetAsync(dctl, 0, sizeof(FlowCtl) * hp.size(), ps);
             if (e == cudaSuccess) e = cudaMemcpyAsync(dg, &hg, sizeof(FlowGlobal), cudaMemcpyHostToDevice, ps);
             if (e == cudaSuccess) e = cudaMemcpyAsync(dhome, home.data(), sizeof(int) * grid, cudaMemcpyHostToDevice, ps);
@@ -894,7 +1095,8 @@ extern "C" mlb_status mlb_batch_solve(const mlb_opts* opts, mlb_batch_problem* p
         else if (hg.err) flow_err(MLB_ETIMEOUT, "batch_flow_pcg_kernel: no problem made progress within the wait limit");
         cudaStreamDestroy(ps);
     }
-    for (void* q : {(void*)dp, (void*)dctl, (void*)dg, (void*)dpart, (void*)dhome})
+    for (void* q : {(void*)dp, (void*)dctl, (void*)dg, (void*)dpart, (void*)dsymItem, (void*)drowpart, (void*)dcolpart,
+                    (void*)dhome})
         if (q) cudaFree(q);
     const int64_t persistent = (first == MLB_OK && !hp.empty()) ? 1 : 0;
     g_batch_phase_ms[1] = ms_since(tp);
