@@ -40,7 +40,7 @@ constexpr int kFlowWarps = kFlowThreads / 32;
 constexpr int kUpdRows = 128;                  // rows per chunk of the vector phases
 constexpr int kFlowDenseRows = 16;             // rows per product chunk, complete patterns (4 rows x 2 column halves per warp pair)
 constexpr int64_t kProdValues = 1 << 18;       // panel values per product chunk, truncated patterns
-constexpr int kFlowSymSeg = 256;               // columns per product chunk, symmetric storage (4 tiles)
+constexpr int kFlowSymSeg = 512;               // columns per product chunk, symmetric storage (8 tiles)
 // shared scratch of a symmetric chunk, in doubles: p on the rows and columns
 // in FP64 and in FP32 high and low parts, and eight warps' column sums
 constexpr int kFlowSymSmem = (kSymRows + kFlowSymSeg) + (kSymRows + kFlowSymSeg) + 8 * 256 / 2;
