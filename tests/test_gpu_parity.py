@@ -423,10 +423,9 @@ def test_batch_solve_matches_oracle(pkg, prec, tol):
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", MIXED_TOL)])
 def test_batch_solve_mixed_sizes_dense_oracle(pkg, prec, tol):
-    """A batch with systems on both sides of the persistent-launch size limit
-    (1,024 unknowns): the small ones run one CTA each, the large one the
-    full-grid PCG on the stream pool.  tau = infinity, so each must equal the
-    dense BLUP of its own data."""
+    """A batch of systems of different sizes in the persistent dataflow launch
+    (tau = infinity: symmetric chunks in the mixed path, dense row panels in
+    FP64); each must equal the dense BLUP of its own data."""
     from paper_1701_00285_gb300.binding import batch_solve
     small = [q for q in wl.batched_problems(count=40) if q.N <= 1000][:2]
     big = wl.small_problem(590, 2600, 3, 1, nu=1.5, rho=0.3, nugget=1e-4, leaf_size=64, M=150)
@@ -440,6 +439,33 @@ def test_batch_solve_mixed_sizes_dense_oracle(pkg, prec, tol):
         assert s == 0 and its > 0, q.name
         ref = dense.dense_blup(q.points, q.Z, q.targets[:150], q.w, q.nu, q.rho, q.nugget)
         assert rel(y, ref["yhat"]) < tol, (q.name, prec)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-6)])
+def test_batch_solve_wide_system_on_stream_pool(pkg, prec, tol):
+    """A system wider than the persistent launch takes (12,288 unknowns) runs
+    the single-problem PCG on the stream pool while two small ones run in the
+    launch: the wide one must agree with the same problem solved alone."""
+    from paper_1701_00285_gb300.binding import batch_solve
+    small = [q for q in wl.batched_problems(count=40) if q.N <= 1000][:2]
+    wide = wl.small_problem(591, 13000, 3, 1, nu=1.5, rho=0.2, nugget=1e-4, leaf_size=64, M=100)
+    probs = small + [wide]
+    items = [{"points": q.points, "w": q.w, "nu": q.nu, "rho": q.rho, "nugget": q.nugget,
+              "tau_factor": math.inf, "Z": q.Z, "targets": q.targets[:100]} for q in probs]
+    res, ms, st = batch_solve(items, precision=prec, pcg_rtol=1e-10, pcg_maxit=50000)
+    from paper_1701_00285_gb300 import lib
+    assert st == 0, lib().mlb_batch_last_error().decode()
+    assert wide.N - (wide.d + 1) > 12288
+    ctx = ctx_for(pkg, wide, prec, rtol=1e-10, pcg_maxit=50000)
+    ctx.assemble(wide.nu, wide.rho, wide.nugget, math.inf)
+    beta, info = ctx.solve(wide.Z)
+    yref = ctx.predict(wide.targets[:100])
+    y, b, s, its = res[2]
+    assert s == 0 and its > 0
+    assert rel(y, yref) < tol
+    for q, (y, b, s, its) in zip(small, res[:2]):
+        ref = dense.dense_blup(q.points, q.Z, q.targets[:100], q.w, q.nu, q.rho, q.nugget)
+        assert s == 0 and rel(y, ref["yhat"]) < (1e-8 if prec == "fp64" else MIXED_TOL), q.name
 
 
 # ---- kriging mean squared error ---------------------------------------------------
