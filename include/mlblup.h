@@ -214,8 +214,11 @@ typedef struct {
 /* Solves `count` independent multilevel BLUP problems (each: basis, assembly,
  * diagonal PCG, trend step, predictions, as for a single context with
  * `opts`).  Problems may differ in n, d, w, theta and tau.  The setup and
- * closing phases run on `host_threads` streams in parallel; the PCG solves of
- * all problems run in one persistent launch, one CTA per problem.  Returns
+ * closing phases run on `host_threads` streams in parallel.  The PCG solves
+ * of all problems of at most 12,288 unknowns run in one persistent launch,
+ * their iterations cut into chunks that any CTA may take; wider systems run
+ * the single-problem PCG on the stream pool meanwhile.  Results do not depend
+ * on the scheduling: every reduction has a fixed order.  Returns
  * MLB_OK if every problem succeeded, else the first failing status (each
  * problem's own status is in probs[i].status).  ms_out (may be NULL): wall
  * time of the call.  opts->matrix_free must be 0. */
