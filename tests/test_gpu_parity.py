@@ -468,6 +468,36 @@ def test_batch_solve_wide_system_on_stream_pool(pkg, prec, tol):
         assert s == 0 and rel(y, ref["yhat"]) < (1e-8 if prec == "fp64" else MIXED_TOL), q.name
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_solve_edge_cases(pkg, prec):
+    """Edge cases of the persistent launch, beside a regular problem:
+    - a system of one 128-row block (no column pieces);
+    - data in the trend space, so Z_W is zero up to rounding and the
+      predictions are the trend alone;
+    - a one-leaf problem whose N is one more than p (a single wavelet)."""
+    from paper_1701_00285_gb300.binding import batch_solve
+    regular = wl.small_problem(592, 1500, 2, 1, nu=1.5, rho=0.3, nugget=1e-4, leaf_size=64, M=40)
+    tiny = wl.small_problem(593, 100, 2, 1, nu=0.5, rho=0.2, nugget=1e-4, leaf_size=128, M=40)
+    flat = wl.small_problem(594, 700, 3, 1, nu=2.5, rho=0.3, nugget=1e-4, leaf_size=64, M=40)
+    lo, hi = design.box(flat.points)
+    beta_true = np.random.default_rng(5).standard_normal(4)
+    flat_Z = design.design_matrix(flat.points, 1, lo, hi) @ beta_true
+    single = wl.small_problem(595, 4, 2, 1, nu=1.5, rho=0.3, nugget=1e-2, leaf_size=64, M=10)
+    probs = [regular, tiny, flat, single]
+    Zs = [regular.Z, tiny.Z, flat_Z, single.Z]
+    items = [{"points": q.points, "w": q.w, "nu": q.nu, "rho": q.rho, "nugget": q.nugget,
+              "tau_factor": math.inf, "Z": z, "targets": q.targets} for q, z in zip(probs, Zs)]
+    res, ms, st = batch_solve(items, precision=prec, pcg_rtol=1e-12, pcg_maxit=50000)
+    from paper_1701_00285_gb300 import lib
+    assert st == 0, lib().mlb_batch_last_error().decode()
+    tol = 1e-9 if prec == "fp64" else MIXED_TOL
+    for q, z, (y, b, s, its) in zip(probs, Zs, res):
+        ref = dense.dense_blup(q.points, z, q.targets, q.w, q.nu, q.rho, q.nugget)
+        assert s == 0, q.name
+        assert rel(y, ref["yhat"]) < tol, (q.name, prec)
+    np.testing.assert_allclose(res[2][1], beta_true, rtol=1e-8, atol=1e-8)
+
+
 # ---- kriging mean squared error ---------------------------------------------------
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("mixed", 1e-5)])
