@@ -92,9 +92,10 @@ struct FlowProblem {
 struct FlowCtl {
     unsigned long long ticket;
     unsigned done;             // chunks of the current epoch finished
-    int finished;
+    int finished;              // set when the problem's solve ended (the search needs no flag:
+                               // a finished problem shows no open chunk)
     double rz, bb, rr, alpha, beta;
-    int it;
+    int it;                    // iterations completed
 };
 
 struct FlowGlobal {
