@@ -269,7 +269,7 @@ def run_reference(args, rank, world):
         return
     P = workload(args)
     for _ in range(max(0, args.warmup)):
-        cpu_baseline(P, sizes=ORACLE_SIZES[:1])
+        cpu_baseline(P, sizes=ORACLE_SIZES[:2])     # two sizes: the fit stays defined
     runs = [cpu_baseline(P) for _ in range(args.steps)]
     value = float(np.median([r["value"] for r in runs]))
     cb = runs[-1]
